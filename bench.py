@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Replica-exchange LJ MD throughput on GB300: replica·atom-steps/s and exch/s.
+
+Default workload (one GPU): 64 replicas x 864 atoms, reduced density 0.8442,
+temperatures geometric 0.7-2.0, exchange stride N_x = 10, Verlet skin 0.3,
+rc = 2.5, dt = 0.005, SVR tau 0.5, FCC start; mixed-precision batched path.
+One bench step = every replica advances N_x MD steps (one persistent launch)
++ one exchange attempt (one launch).  The plain FP64 one-replica-per-launch
+path is timed on the same workload for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config c1]
+
+Under torchrun each rank runs its own ensemble (different seed, no data-path
+collective): weak scaling.  --impl reference times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0812_1633_gb300 import inputs  # noqa: E402
+
+CONFIGS = {
+    # name: (description, list of ensembles (N, R, t_min, t_max), nx, skin, budget mode)
+    "c0": ("8 replicas x 256 atoms, rho 0.8442, T 0.8-1.6 geometric, N_x 100",
+           [(256, 8, 0.8, 1.6)], 100, 0.5, "fixed", "fp64"),
+    "c1": ("64 replicas x 864 atoms, rho 0.8442, T 0.7-2.0 geometric, N_x 10, skin 0.3",
+           [(864, 64, 0.7, 2.0)], 10, 0.3, "fixed", "mixed"),
+    "c2": ("5 ensembles in one launch: 16x256, 32x500, 48x864, 64x2048, 96x4000 atoms, T 0.7-2.5, "
+           "budgets uniform 5-50 per replica per attempt",
+           [(256, 16, 0.7, 2.5), (500, 32, 0.7, 2.5), (864, 48, 0.7, 2.5), (2048, 64, 0.7, 2.5),
+            (4000, 96, 0.7, 2.5)], 0, 0.5, "random", "mixed"),
+    "c3": ("256 replicas x 4000 atoms, rho 0.8442, T 0.75-1.8 geometric, N_x 10",
+           [(4000, 256, 0.75, 1.8)], 10, 0.5, "fixed", "mixed"),
+    "c4": ("1024 replicas x 2048 atoms, rho 0.8442, T 0.7-3.0 geometric, N_x 1",
+           [(2048, 1024, 0.7, 3.0)], 1, 0.5, "fixed", "mixed"),
+}
+FLOPS_PER_PAIR = 37.0   # unique pair: 34 for the pair itself + 3 for the reaction
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_budgets(cfg, R, cycles, seed):
+    _, ens, nx, _, mode, _ = cfg
+    if mode == "random":
+        return inputs.random_budgets(R, cycles, 5, 50, seed)
+    return np.full((cycles, R), nx, dtype=np.int32)
+
+
+def atoms_per_cycle(cfg, budgets_row):
+    Ns = np.concatenate([[N] * R for (N, R, _, _) in cfg[1]])
+    return float((Ns * budgets_row).sum())
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_rate(cfg, seed, wall_target=10.0, max_steps=2000):
+    """Replica·atom-steps/s of the FP64 CPU oracle on this host's cores."""
+    import oracle as O
+    nthreads = os.cpu_count() or 1
+    ens_list = []
+    for i, (N, R, t0, t1) in enumerate(cfg[1]):
+        L = inputs.box_length(N)
+        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=cfg[3]))
+    steps = 2
+    done_atoms, spent = 0.0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        for e in ens_list:
+            e.advance([steps] * e.R, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        done_atoms += steps * sum(e.R * e.reps[0].N for e in ens_list)
+        spent += dt
+        if spent >= wall_target or steps >= max_steps:
+            break
+        steps = int(min(max_steps, max(steps * 2, steps * wall_target / max(dt, 1e-3) * 0.5)))
+    sample = (f"{'+'.join(f'{e.R}x{e.reps[0].N}' for e in ens_list)} replicas x atoms, "
+              f"{int(done_atoms / sum(e.R * e.reps[0].N for e in ens_list))} MD steps each from the "
+              f"FCC start, {spent:.1f} s wall")
+    return done_atoms / spent, nthreads, sample
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    nthreads = os.cpu_count() or 1
+    seed = 12345 + 1
+    ens_list = []
+    for i, (N, R, t0, t1) in enumerate(cfg[1]):
+        L = inputs.box_length(N)
+        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=cfg[3]))
+    Rtot = sum(e.R for e in ens_list)
+    # each reference step: the whole workload's cycle for small configs; a
+    # bounded sample of replicas for large ones (size-normalised metric)
+    cap_atoms = 600_000
+    sub = []
+    for e in ens_list:
+        k = max(1, min(e.R, cap_atoms // max(1, e.reps[0].N * len(ens_list))))
+        sub.append(k)
+    budgets = make_budgets(cfg, Rtot, args.warmup + args.steps, 7)
+    times, work = [], 0.0
+    for c in range(args.warmup + args.steps):
+        off = 0
+        t0 = time.perf_counter()
+        w = 0.0
+        for e, k in zip(ens_list, sub):
+            b = budgets[c][off:off + e.R].copy()
+            b[k:] = 0
+            e.advance(b, nthreads=nthreads)
+            e.exchange()
+            w += float(b.sum()) * e.reps[0].N
+            off += e.R
+        dt = time.perf_counter() - t0
+        if c >= args.warmup:
+            times.append(dt)
+            work += w
+    total = sum(times)
+    value = work / total
+    line = {
+        "impl": "reference", "metric": "replica·atom-steps/s", "value": value,
+        "unit": "replica·atom-steps/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (FCC start, seeded Philox velocities)",
+        "config": {"workload": cfg[0], "replicas_timed": sub},
+        "cpu_baseline": {"value": value, "unit": "replica·atom-steps/s", "cores": nthreads,
+                         "kind": "oracle",
+                         "sample": f"per step: {'+'.join(str(k) for k in sub)} replicas of the workload "
+                                   f"advance their stride and attempt one exchange"},
+        "e2e": {"value": value, "unit": "replica·atom-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """SM clock and throttle reasons sampled every ~1 ms during the timed region
+    through NVML (read-only queries via ctypes); nvidia-smi polling as fallback."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes as C
+        import threading
+        self.C, self.threading = C, threading
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.nvml = self.h = None
+        try:
+            import torch
+            bus = torch.cuda.get_device_properties(cuda_index).pci_bus_id
+        except Exception:
+            bus = None
+        try:
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() == 0:
+                h = C.c_void_p()
+                ok = -1
+                if bus:
+                    ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(h))
+                if ok != 0:
+                    ok = nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(cuda_index), C.byref(h))
+                if ok == 0:
+                    self.nvml, self.h = nv, h
+                    m = C.c_uint()
+                    if nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(m)) == 0:
+                        self.max_mhz = float(m.value)
+        except OSError:
+            pass
+
+    def _poll(self):
+        C = self.C
+        mhz, rs = C.c_uint(), C.c_ulonglong()
+        get_r = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) == 0:
+                self.samples.append(float(mhz.value))
+            if get_r(self.h, C.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.001)
+
+    def __enter__(self):
+        if self.nvml is not None:
+            self.stop = self.threading.Event()
+            self.t = self.threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.nvml is not None:
+            self.stop.set()
+            self.t.join()
+
+    def summary(self):
+        if self.nvml is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["NVML unavailable"]}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples),
+                "source": "NVML, 1 ms period, during the timed steps"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def in_cutoff_pairs_per_atom(x, cfg, n_sample=8, rc=2.5):
+    """Mean unique in-cutoff pairs per atom over a sample of replicas (from a state)."""
+    tot_pairs = tot_atoms = 0
+    off = 0
+    for (N, R, _, _) in cfg[1]:
+        L = inputs.box_length(N)
+        for r in range(min(R, n_sample)):
+            p = x[off + r * N: off + (r + 1) * N]
+            cnt = 0
+            for i0 in range(0, N, 512):
+                d = p[None, :, :] - p[i0:i0 + 512, None, :]
+                d -= L * np.rint(d / L)
+                r2 = (d * d).sum(-1)
+                cnt += int((r2 < rc * rc).sum()) - min(512, N - i0)
+            tot_pairs += cnt / 2
+            tot_atoms += N
+        off += N * R
+    return tot_pairs / tot_atoms
+
+
+def run_gpu(args, cfg):
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    re.lib()
+    desc, ens_spec, nx, skin, mode, prec = cfg
+    seed = 12345 + 1 + 1000 * rank
+    members = []
+    for i, (N, R, t0, t1) in enumerate(ens_spec):
+        L = inputs.box_length(N)
+        members.append(re.Context(N, L, 2.5, inputs.geometric_ladder(t0, t1, R), seed + i,
+                                  skin=skin, precision=prec, nx=max(nx, 1)))
+    ctx = members[0] if len(members) == 1 else re.Context.group(members)
+    if len(members) > 1:
+        for m in members:
+            m.close()
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    if args.launch:
+        cl, th, cd = (int(v) for v in args.launch.split(","))
+        members_kw = dict(cluster=cl, threads=th, cell_div=cd)
+        ctx.close()
+        members = []
+        for i, (N, R, t0, t1) in enumerate(ens_spec):
+            L = inputs.box_length(N)
+            members.append(re.Context(N, L, 2.5, inputs.geometric_ladder(t0, t1, R), seed + i,
+                                      skin=skin, precision=prec, nx=max(nx, 1), **members_kw))
+        ctx = members[0] if len(members) == 1 else re.Context.group(members)
+        if len(members) > 1:
+            for m in members:
+                m.close()
+        ctx.set_stream(stream)
+        tuned = ctx.config()
+    else:
+        tuned = ctx.autotune(steps=max(5, min(20, nx if nx else 20)))
+    Rtot = ctx.n_rep
+    W, K = args.warmup, args.steps
+    budgets = make_budgets(cfg, Rtot, W + K, 7 + rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def cycle(c):
+        ctx.advance(budgets[c])
+        ctx.exchange()
+
+    for c in range(W):
+        cycle(c)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(K):
+            flush.zero_()   # L2 flush between timed steps (outside the timed events)
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            ctx.advance(budgets[W + k])
+            e1.record(stream)
+            ctx.exchange()
+            e2.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    adv_ms = [a.elapsed_time(b) for a, b, c in ev]
+    exch_ms = [b.elapsed_time(c) for a, b, c in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    work = sum(atoms_per_cycle(cfg, budgets[W + k]) for k in range(K))
+    value = ws * work / total_s
+    n_ens = len(ens_spec)
+    exch_per_s = ws * n_ens * K / total_s
+    pairs_per_attempt = sum((R - 1 - (a & 1)) // 2 + 1 if R > 1 else 0
+                            for (N, R, _, _) in ens_spec for a in range(2)) / 2
+
+    # ---- roofline of the dominant kernel (the batched MD launch)
+    x, _ = ctx.get_state()
+    pairs = in_cutoff_pairs_per_atom(x, cfg)
+    adv_mean_s = statistics.mean(adv_ms) / 1e3
+    flops_per_launch = FLOPS_PER_PAIR * pairs * work / K
+    achieved = flops_per_launch / adv_mean_s / 1e12
+
+    # ---- e2e: public API with host buffers every step
+    t_e2e0 = time.perf_counter()
+    nE = max(3, min(K, 20))
+    for k in range(nE):
+        ctx.advance(budgets[W + (k % K)])
+        ctx.exchange(outputs=True)
+        ctx.energies()
+    t_e2e = time.perf_counter() - t_e2e0
+    e2e_work = sum(atoms_per_cycle(cfg, budgets[W + (k % K)]) for k in range(nE))
+    h2d = 4 * Rtot
+    d2h = 4 * Rtot + Rtot + 3 * 8 * Rtot + 4 * Rtot
+
+    # ---- plain FP64 one-replica-per-launch path on the same workload (bounded)
+    plain = None
+    if len(ens_spec) == 1 and rank == 0 and not args.no_plain:
+        N, R, t0, t1 = ens_spec[0]
+        L = inputs.box_length(N)
+        p = re.Context(N, L, 2.5, inputs.geometric_ladder(t0, t1, R), seed, skin=skin,
+                       path="plain", nx=max(nx, 1))
+        p.set_stream(stream)
+        p.advance(budgets[0])
+        p.exchange()
+        torch.cuda.synchronize()
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nP = 2
+        pe0.record(stream)
+        for k in range(nP):
+            p.advance(budgets[W + k])
+            p.exchange()
+        pe1.record(stream)
+        torch.cuda.synchronize()
+        pt = pe0.elapsed_time(pe1) / 1e3
+        pw = sum(atoms_per_cycle(cfg, budgets[W + k]) for k in range(nP))
+        plain = {"value": pw / pt, "unit": "replica·atom-steps/s", "steps": nP,
+                 "speedup_of_batched_mixed": value / ws / (pw / pt)}
+        p.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_rate(cfg, seed, wall_target=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "replica·atom-steps/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": "replica·atom-steps/s", "value": value, "unit": "replica·atom-steps/s",
+            "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": 1e3 * total_s / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (FCC start at rho 0.8442, seeded Philox velocities and budgets)",
+            "config": {"workload": desc, "path": f"{prec} batched (one persistent launch per cycle)",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "launch": tuned, "parallelism": f"replicas, {ws} independent ensemble(s)"},
+            "exch_per_s": exch_per_s,
+            "pair_attempts_per_s": exch_per_s * pairs_per_attempt / max(n_ens, 1),
+            "advance_ms": statistics.mean(adv_ms), "exchange_ms": statistics.mean(exch_ms),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "md_batched_kernel<mixed>",
+                         "algorithmic": f"{FLOPS_PER_PAIR:.0f} flop x {pairs:.2f} unique in-cutoff "
+                                        f"pairs per atom-step"},
+            "plain_fp64": plain,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * e2e_work / t_e2e, "unit": "replica·atom-steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c1", choices=sorted(CONFIGS))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--launch", default=None,
+                    help="fixed launch shape 'cluster,threads,cell_div' instead of the autotuner")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+    else:
+        run_gpu(args, cfg)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * re.h -- C ABI of the GB300 (sm_103a) asynchronous replica-exchange
+ * Lennard-Jones molecular-dynamics library.
+ *
+ * Method: G. Bussi, "A simple asynchronous replica-exchange implementation",
+ * arXiv:0812.1633.  Replicas of an LJ liquid run velocity-Verlet MD with the
+ * stochastic-velocity-rescaling thermostat (Example section) at different
+ * temperatures; exchanges swap temperatures, not coordinates, with a
+ * Metropolis test on the lower-rank replica's uniform number, and rescale
+ * velocities by sqrt(T_new/T_old) (Implementation section).  Replicas may
+ * perform different numbers of steps between attempts (asynchronous stride,
+ * Example section).
+ *
+ * Conventions for every entry point:
+ *   - Units: LJ reduced units (sigma = epsilon = m = k_B = 1).
+ *   - Host arrays are owned by the caller; inputs are copied during the call,
+ *     outputs are written before the call returns.  Array lengths are given
+ *     per argument.  Device arrays ("_device" entry points) are owned by the
+ *     caller and must stay valid until the work on the given stream is done.
+ *   - Replica order: replicas of a context are numbered 0..n_rep-1; in a group
+ *     (re_group) the replicas of its members follow one another in member order.
+ *   - Positions/velocities/forces: doubles, AoS per replica, [replica][atom][xyz].
+ *   - Return value: RE_OK (0) or a negative RE_E* code; re_last_error() gives
+ *     a one-line message.  Errors raised by device work of an asynchronous
+ *     call (list overflow, non-finite energy) are reported by the next call
+ *     that synchronises (getters, re_sync).
+ *   - Threads: one host thread per context at a time.  Calls are queued on the
+ *     context's CUDA stream (re_set_stream); getters synchronise that stream.
+ *   - The library allocates its own device memory with cudaMalloc at creation.
+ *
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11) used as a
+ * counter-based generator; key = (seed, stream), counter = (index, tag, sub, 0):
+ *   tag 1 initial velocities  (stream = replica id, index = atom)
+ *   tag 2 thermostat Gaussian (stream = replica id, index = step)
+ *   tag 3 thermostat Gamma trials (stream = replica id, index = step, sub = trial)
+ *   tag 4 Metropolis uniform  (stream = replica id, index = attempt)
+ *   tag 5 random pair offset  (stream = 2^64-1, index = attempt)
+ * A uniform is (word >> 11) * 2^-53.
+ */
+#ifndef RE_GB300_H
+#define RE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RE_OK 0
+#define RE_EINVAL (-1)    /* bad argument (see re_last_error)                 */
+#define RE_ECUDA (-2)     /* CUDA runtime error                               */
+#define RE_ENOMEM (-3)    /* device allocation failed                         */
+#define RE_ENUMERIC (-4)  /* non-finite energy in some replica                */
+#define RE_EOVERFLOW (-5) /* neighbour list or scratch capacity exceeded      */
+#define RE_ETIMEOUT (-6)  /* a bounded device wait gave up                    */
+
+#define RE_PREC_FP64 0    /* FP64 pair forces                                 */
+#define RE_PREC_MIXED 1   /* FP32 pair forces, FP64 accumulation and state    */
+
+#define RE_PATH_BATCHED 0 /* one persistent launch runs every replica's budget */
+#define RE_PATH_PLAIN 1   /* per replica and per step a sequence of launches  */
+
+typedef struct re_ctx re_ctx; /* opaque; created by re_create/re_group, freed by re_destroy */
+
+typedef struct re_opts {
+  double dt;        /* time step; default 0.005 (Example section)                    */
+  double skin;      /* Verlet skin; list radius rc + skin; default 0.5 (list to 3.0) */
+  double tau_T;     /* thermostat relaxation time; default 0.5; <= 0: NVE            */
+  int shift_energy; /* 1 (default): pair energy shifted to 0 at rc; 0: truncated      */
+  int precision;    /* RE_PREC_MIXED (default) or RE_PREC_FP64                        */
+  int path;         /* RE_PATH_BATCHED (default) or RE_PATH_PLAIN                     */
+  int pair_parity;  /* 0 (default): first pair offset alternates 0,1; 1: random      */
+  int nx;           /* steps per replica used by re_advance(c, NULL); default 10      */
+  int nbr_capacity; /* neighbours per atom (multiple of 4); 0: from the density        */
+  int cell_div;     /* list cells per list radius (1..3); 0: automatic               */
+  int cluster;      /* CTAs cooperating on one replica (1, 2, 4, 8); 0: automatic     */
+  int threads;      /* threads per CTA (64..512, multiple of 32); 0: automatic        */
+} re_opts;
+
+/* Fills *o with the defaults listed above. */
+void re_default_opts(re_opts *o);
+
+/* Creates one ensemble of n_rep replicas of N atoms in a cubic periodic box of
+ * side L with LJ cutoff rc.  Replica k starts at temperature temps[k] on an
+ * FCC lattice (N must be 4 k^3) with Maxwell-Boltzmann velocities drawn from
+ * seed, centre-of-mass motion removed and rescaled to exactly temps[k]
+ * (3N - 3 degrees of freedom).  temps: n_rep distinct positive values (host).
+ * opt: NULL for defaults.  Requires rc + skin < L/2, N <= 65535 for the
+ * batched path.  *out receives the new context. */
+int re_create(int N, double L, double rc, int n_rep, const double *temps, uint64_t seed,
+              const re_opts *opt, re_ctx **out);
+
+/* Builds one context holding the replicas of n contexts (ensembles of uneven
+ * sizes), so that one launch advances all of them.  The members are copied;
+ * they stay valid and independent.  All members must share precision and
+ * path.  Exchanges never mix ensembles. */
+int re_group(re_ctx *const *ctxs, int n, re_ctx **out);
+
+/* Advances replica k by steps[k] MD steps (k over all replicas of the
+ * context; host array; NULL: opt.nx for every replica).  Each step: half
+ * kick, drift, list rebuild if some atom moved more than skin/2 since the
+ * last rebuild, LJ forces, half kick, thermostat.  Asynchronous. */
+int re_advance(re_ctx *c, const int32_t *steps);
+
+/* One exchange attempt in every ensemble: temperatures sorted, sorted
+ * neighbours paired from offset 0 or 1, Metropolis with the lower replica
+ * id's uniform, accepted pairs swap T and rescale velocities.  Outputs (host,
+ * n_rep each, may be NULL): partner id or -1, accepted flag.  Synchronises
+ * only when an output is requested. */
+int re_exchange(re_ctx *c, int32_t *partner_out, uint8_t *accepted_out);
+
+/* n_cycles times { re_advance(steps + cycle * n_rep); re_exchange }.  steps:
+ * host array n_cycles * n_rep, or NULL for opt.nx.  use_graph != 0 captures
+ * the launches of all cycles in one CUDA graph and replays it. */
+int re_run(re_ctx *c, int n_cycles, const int32_t *steps, int use_graph);
+
+/* Per replica (host, n_rep each, K and H may be NULL): potential energy U,
+ * kinetic energy K and H~ = U + K + (energy removed by the thermostat). */
+int re_energies(re_ctx *c, double *U, double *K, double *H);
+/* Current temperature of every replica (host, n_rep). */
+int re_temps(re_ctx *c, double *T);
+/* Positions (wrapped into [0, L)) and velocities, host arrays of
+ * 3 * (atoms of all replicas) doubles each; either may be NULL. */
+int re_get_state(re_ctx *c, double *x, double *v);
+/* Replaces positions and velocities (same layout); lists and forces are
+ * recomputed before the next step.  Step counters are unchanged. */
+int re_set_state(re_ctx *c, const double *x, const double *v);
+/* Forces at the current positions (host, 3 * atoms). */
+int re_forces(re_ctx *c, double *f);
+/* Per replica steps done and list rebuilds done (host, n_rep each; may be NULL). */
+int re_counters(re_ctx *c, int64_t *steps, int64_t *rebuilds);
+/* Per ensemble and per sorted-temperature pair position k (k = 0..R_e-2), the
+ * number of attempts and of accepted exchanges; ensembles concatenated,
+ * sum over ensembles of (R_e - 1) entries. */
+int re_accept_stats(re_ctx *c, int64_t *attempts, int64_t *accepts);
+/* Shape of the context: replicas, atoms of all replicas, ensembles, pair
+ * stats entries (any may be NULL). */
+int re_info(const re_ctx *c, int *n_rep, int64_t *n_atoms, int *n_ens, int *n_pairs);
+/* Launch configuration in use: cluster, threads, cell_div (any may be NULL). */
+int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div);
+/* Times candidate launch configurations (cluster, threads, cell_div) over
+ * `steps` steps each on a copy of the state and keeps the fastest; the state
+ * is restored afterwards. */
+int re_autotune(re_ctx *c, int steps);
+/* Queues subsequent work on stream (a cudaStream_t; NULL: legacy default). */
+int re_set_stream(re_ctx *c, void *stream);
+/* Waits for the context's queued work and reports deferred device errors. */
+int re_sync(re_ctx *c);
+/* Last error message of the context (or of the last failed create when c is NULL). */
+const char *re_last_error(const re_ctx *c);
+void re_destroy(re_ctx *c);
+
+/* ---------------------------------------------------------------------------
+ * Stateless device entry points (device pointers, caller-owned, on `stream`).
+ */
+
+/* One exchange attempt over R <= 4096 replicas (Implementation section), as
+ * in re_exchange: T, U device arrays (R doubles); outputs T_out (R doubles,
+ * new temperatures), partner (R int32, -1 if unpaired), accepted (R uint8),
+ * vscale (R doubles, sqrt(T_new/T_old) or 1).  T must hold distinct values. */
+int re_exchange_device(int R, const double *T, const double *U, uint64_t seed, int64_t attempt,
+                       int parity_mode, double *T_out, int32_t *partner, uint8_t *accepted,
+                       double *vscale, void *stream);
+
+/* Truncated LJ forces and potential energy of N atoms in a cubic periodic box
+ * of side L with cutoff rc (Example section): x device array of 3N doubles
+ * (AoS), f device array of 3N doubles, U device pointer to one double.
+ * Pairs are found with the same cell binning and neighbour-list kernels as
+ * the MD path (list radius rc + skin, skin = 0.5).  precision: RE_PREC_FP64
+ * or RE_PREC_MIXED.  Scratch (cells, lists) is allocated with cudaMalloc and
+ * freed before return; the call synchronises `stream`.  Requires 2 <= N <=
+ * 65535 and rc + 0.5 < L/2. */
+int re_lj_forces_device(int N, double L, double rc, int shift, int precision, const double *x,
+                        double *f, double *U, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

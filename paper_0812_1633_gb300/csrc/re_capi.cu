@@ -1,0 +1,947 @@
+// re_capi.cu -- host side of the C ABI declared in include/re.h: contexts,
+// device memory, launch configuration, the advance / exchange loop (optionally
+// captured in a CUDA graph), getters, the autotuner and the stateless entry
+// points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "re.h"
+#include "re_internal.h"
+
+using re::EnsDev;
+using re::LaunchCfg;
+using re::RepDev;
+using re::StateDev;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kRing = 8;  // pinned staging slots for per-call budgets
+
+struct Ensemble {
+  int N, R;
+  double L, rc;
+  std::vector<double> temps;
+  uint64_t seed;
+};
+
+}  // namespace
+
+struct re_ctx {
+  re_opts opt{};
+  std::vector<EnsDev> ens;
+  std::vector<RepDev> reps;
+  int n_rep = 0, n_pairs = 0;
+  int64_t n_atoms = 0, n_nbr = 0;
+  int max_n = 0, max_r = 0, max_ncell = 0;
+  LaunchCfg cfg{1, 256, 0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  StateDev s{};
+  EnsDev* d_ens = nullptr;
+  RepDev* d_rep = nullptr;
+  int* d_work = nullptr;
+  int32_t* d_budget = nullptr;      // n_rep, per call
+  int32_t* d_budget_nx = nullptr;   // n_rep, filled with opt.nx
+  int32_t* d_budget_run = nullptr;  // n_cycles * n_rep for re_run
+  size_t budget_run_cap = 0;
+  int32_t* h_ring = nullptr;        // pinned, kRing * n_rep
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_pos = 0;
+  int32_t* d_partner = nullptr;
+  uint8_t* d_acc = nullptr;
+  double* d_io = nullptr;           // 3 * n_atoms doubles, state import/export
+  bool plain_refresh = true;        // plain path: lists/forces need a prologue
+  std::vector<void*> allocs;
+  std::string err;
+  // cached graph of re_run
+  cudaGraphExec_t graph = nullptr;
+  int graph_cycles = 0;
+  const int32_t* graph_budget = nullptr;
+};
+
+namespace {
+
+int fail(re_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(re_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? RE_ENOMEM : RE_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define RE_CUDA(c, call, what)                   \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+template <class T>
+int dalloc(re_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return RE_OK;
+}
+
+// List cells: nc = floor(L / (rlist / m)) cells per side scanned over a
+// (2m + 1)^3 neighbourhood; cells only pay when 2m + 1 < nc.  m is chosen
+// to minimise candidates per atom plus a per-cell visiting cost.
+void choose_cells(double L, double rlist, int N, int want_m, int* nc_out, int* m_out) {
+  double best = (double)N;  // all pairs
+  int bnc = 0, bm = 0;
+  for (int m = 1; m <= 3; ++m) {
+    if (want_m > 0 && m != want_m) continue;
+    const int nc = (int)std::floor(L / (rlist / m));
+    if (nc < 2 * m + 2 || nc * nc * nc > 65535) continue;
+    const double span = 2.0 * m + 1.0;
+    const double cost = N * span * span * span / ((double)nc * nc * nc) + 4.0 * span * span * span;
+    if (cost < best) {
+      best = cost;
+      bnc = nc;
+      bm = m;
+    }
+  }
+  *nc_out = bnc;
+  *m_out = bm;
+}
+
+int default_capacity(int N, double L, double rlist) {
+  const double rho = N / (L * L * L);
+  const double mean = rho * 4.0 / 3.0 * M_PI * rlist * rlist * rlist;
+  int cap = (int)std::ceil(1.5 * mean + 16.0);
+  cap = (cap + 3) / 4 * 4;
+  cap = std::min(cap, ((N - 1) + 3) / 4 * 4);
+  return std::max(cap, 4);
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+LaunchCfg default_cfg(const re_ctx* c) {
+  LaunchCfg k{};
+  const int sms = sm_count();
+  int cl = c->opt.cluster;
+  if (cl <= 0) {
+    cl = 1;
+    while (cl < 8 && c->n_rep * cl * 2 <= sms * 2 && c->n_rep * (cl * 2) <= sms + sms / 4 &&
+           (c->max_n + cl * 2 - 1) / (cl * 2) >= 64)
+      cl *= 2;
+  }
+  int th = c->opt.threads;
+  if (th <= 0) {
+    const int per = (c->max_n + cl - 1) / cl;
+    th = std::min(512, std::max(64, (per + 31) / 32 * 32));
+  }
+  k.cluster = cl;
+  k.threads = th;
+  k.cell_div = 0;
+  return k;
+}
+
+int upload_tables(re_ctx* c) {
+  RE_CUDA(c, cudaMemcpyAsync(c->d_ens, c->ens.data(), sizeof(EnsDev) * c->ens.size(),
+                             cudaMemcpyHostToDevice, c->stream), "upload ensembles");
+  RE_CUDA(c, cudaMemcpyAsync(c->d_rep, c->reps.data(), sizeof(RepDev) * c->reps.size(),
+                             cudaMemcpyHostToDevice, c->stream), "upload replicas");
+  return RE_OK;
+}
+
+// Allocate device memory for the current ens/reps tables.
+int allocate(re_ctx* c) {
+  const size_t A = (size_t)c->n_atoms, R = (size_t)c->n_rep, E = c->ens.size();
+  StateDev& s = c->s;
+  int rc = RE_OK;
+  if ((rc = dalloc(c, &s.qx, A)) || (rc = dalloc(c, &s.qy, A)) || (rc = dalloc(c, &s.qz, A)) ||
+      (rc = dalloc(c, &s.vx, A)) || (rc = dalloc(c, &s.vy, A)) || (rc = dalloc(c, &s.vz, A)) ||
+      (rc = dalloc(c, &s.fx, A)) || (rc = dalloc(c, &s.fy, A)) || (rc = dalloc(c, &s.fz, A)) ||
+      (rc = dalloc(c, &s.rx, A)) || (rc = dalloc(c, &s.ry, A)) || (rc = dalloc(c, &s.rz, A)) ||
+      (rc = dalloc(c, &s.ncnt, A)) || (rc = dalloc(c, &s.nbr, (size_t)c->n_nbr)) ||
+      (rc = dalloc(c, &s.T, R)) || (rc = dalloc(c, &s.U, R)) || (rc = dalloc(c, &s.K, R)) ||
+      (rc = dalloc(c, &s.econs, R)) || (rc = dalloc(c, &s.vscale, R)) ||
+      (rc = dalloc(c, &s.step, R)) || (rc = dalloc(c, &s.nreb, R)) ||
+      (rc = dalloc(c, &s.status, R)) || (rc = dalloc(c, &s.valid, R)) ||
+      (rc = dalloc(c, &s.attempt, E)) || (rc = dalloc(c, &s.pair_att, (size_t)c->n_pairs)) ||
+      (rc = dalloc(c, &s.pair_acc, (size_t)c->n_pairs)) ||
+      (rc = dalloc(c, &s.red, R * 1024)) || (rc = dalloc(c, &s.dmax, R)) ||
+      (rc = dalloc(c, &c->d_ens, E)) || (rc = dalloc(c, &c->d_rep, R)) ||
+      (rc = dalloc(c, &c->d_work, R)) || (rc = dalloc(c, &c->d_budget, R)) ||
+      (rc = dalloc(c, &c->d_budget_nx, R)) || (rc = dalloc(c, &c->d_partner, R)) ||
+      (rc = dalloc(c, &c->d_acc, R)) || (rc = dalloc(c, &c->d_io, 3 * A)))
+    return rc;
+  RE_CUDA(c, cudaMemsetAsync(s.nbr, 0, sizeof(uint16_t) * (size_t)c->n_nbr, c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.ncnt, 0, sizeof(int32_t) * A, c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.attempt, 0, sizeof(int64_t) * E, c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.pair_att, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.pair_acc, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.dmax, 0, sizeof(uint32_t) * R, c->stream), "memset");
+  RE_CUDA(c, cudaMallocHost(&c->h_ring, sizeof(int32_t) * R * kRing), "cudaMallocHost");
+  for (int k = 0; k < kRing; ++k)
+    RE_CUDA(c, cudaEventCreateWithFlags(&c->ring_ev[k], cudaEventDisableTiming), "event");
+  // work list: replicas by decreasing size (largest clusters start first)
+  std::vector<int> work(R);
+  for (size_t r = 0; r < R; ++r) work[r] = (int)r;
+  std::stable_sort(work.begin(), work.end(), [&](int a, int b) {
+    return c->ens[c->reps[a].ens].N > c->ens[c->reps[b].ens].N;
+  });
+  RE_CUDA(c, cudaMemcpyAsync(c->d_work, work.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
+                             c->stream), "upload work");
+  std::vector<int32_t> nx(R, c->opt.nx);
+  RE_CUDA(c, cudaMemcpyAsync(c->d_budget_nx, nx.data(), sizeof(int32_t) * R,
+                             cudaMemcpyHostToDevice, c->stream), "upload nx");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  return upload_tables(c);
+}
+
+// Fill per-ensemble cells for the current cfg.cell_div; returns max ncell.
+void apply_cells(re_ctx* c, int want_m) {
+  c->max_ncell = 1;
+  for (auto& e : c->ens) {
+    choose_cells(e.L, e.rlist, e.N, want_m, &e.nc, &e.m);
+    c->max_ncell = std::max(c->max_ncell, e.nc > 0 ? e.nc * e.nc * e.nc : 1);
+  }
+}
+
+int check_cfg(re_ctx* c, const LaunchCfg& k) {
+  if (k.cluster != 1 && k.cluster != 2 && k.cluster != 4 && k.cluster != 8)
+    return fail(c, RE_EINVAL, "cluster must be 1, 2, 4 or 8 (got %d)", k.cluster);
+  if (k.threads < 64 || k.threads > 512 || k.threads % 32)
+    return fail(c, RE_EINVAL, "threads must be a multiple of 32 in [64, 512] (got %d)", k.threads);
+  const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
+                                             c->opt.precision == RE_PREC_FP64);
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (maxsm > 0 && smem > (size_t)maxsm)
+    return fail(c, RE_EINVAL, "replica of %d atoms needs %zu bytes of shared memory (max %d)",
+                c->max_n, smem, maxsm);
+  return RE_OK;
+}
+
+int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget) {
+  if (c->opt.path == RE_PATH_BATCHED) {
+    cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
+                                       c->opt.precision == RE_PREC_FP64, c->cfg, c->max_n,
+                                       c->max_ncell, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
+    return RE_OK;
+  }
+  // plain path: one replica after another, a launch sequence per step
+  for (int r = 0; r < c->n_rep; ++r) {
+    const int steps = h_budget ? h_budget[r] : c->opt.nx;
+    if (steps <= 0 && !c->plain_refresh) continue;
+    const RepDev& rd = c->reps[r];
+    cudaError_t e = re::launch_plain_advance(c->s, c->ens[rd.ens], rd, r, c->d_ens, c->d_rep,
+                                             steps, c->max_ncell, c->stream,
+                                             c->plain_refresh ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "plain MD launch");
+  }
+  c->plain_refresh = false;
+  return RE_OK;
+}
+
+int refresh(re_ctx* c) {
+  if (c->opt.path == RE_PATH_BATCHED) {
+    // budget 0 with invalid lists: the kernel's prologue builds lists, forces, U, K
+    RE_CUDA(c, cudaMemsetAsync(c->d_budget, 0, sizeof(int32_t) * c->n_rep, c->stream), "memset");
+    return launch_advance(c, c->d_budget, nullptr);
+  }
+  c->plain_refresh = true;
+  std::vector<int32_t> zero(c->n_rep, 0);
+  return launch_advance(c, nullptr, zero.data());
+}
+
+int status_check(re_ctx* c) {
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  std::vector<int32_t> st(c->n_rep);
+  RE_CUDA(c, cudaMemcpy(st.data(), c->s.status, sizeof(int32_t) * c->n_rep,
+                        cudaMemcpyDeviceToHost), "read status");
+  for (int r = 0; r < c->n_rep; ++r) {
+    if (st[r] & re::kStOverflow)
+      return fail(c, RE_EOVERFLOW, "replica %d: neighbour list capacity %d exceeded", r,
+                  c->ens[c->reps[r].ens].cap);
+    if (st[r] & (re::kStNumeric | re::kStRngCap))
+      return fail(c, RE_ENUMERIC, "replica %d: non-finite energy or thermostat draw", r);
+  }
+  return RE_OK;
+}
+
+int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<re_ctx*>* src) {
+  int rep_off = 0, pair_off = 0;
+  int64_t atom_off = 0, nbr_off = 0;
+  for (size_t k = 0; k < es.size(); ++k) {
+    const Ensemble& s = es[k];
+    EnsDev e{};
+    e.N = s.N;
+    e.R = s.R;
+    e.rep_off = rep_off;
+    e.pair_off = pair_off;
+    e.L = s.L;
+    e.rc = s.rc;
+    e.skin = c->opt.skin;
+    e.rlist = s.rc + c->opt.skin;
+    e.dt = c->opt.dt;
+    e.tau = c->opt.tau_T;
+    e.shift = c->opt.shift_energy ? 1 : 0;
+    e.parity_mode = c->opt.pair_parity;
+    e.seed = s.seed;
+    e.cap = c->opt.nbr_capacity > 0 ? (c->opt.nbr_capacity + 3) / 4 * 4
+                                    : default_capacity(s.N, s.L, e.rlist);
+    if (src) e.cap = (*src)[k]->ens[0].cap;
+    c->ens.push_back(e);
+    for (int r = 0; r < s.R; ++r) {
+      RepDev rd{};
+      rd.ens = (int)k;
+      rd.id = r;
+      rd.atom_off = (int)atom_off;
+      rd.nbr_off = nbr_off;
+      c->reps.push_back(rd);
+      atom_off += s.N;
+      nbr_off += (int64_t)e.cap * s.N;
+    }
+    rep_off += s.R;
+    pair_off += std::max(0, s.R - 1);
+    c->max_n = std::max(c->max_n, s.N);
+    c->max_r = std::max(c->max_r, s.R);
+  }
+  if (atom_off > INT32_MAX) return fail(c, RE_EINVAL, "too many atoms in one context");
+  c->n_rep = rep_off;
+  c->n_pairs = pair_off;
+  c->n_atoms = atom_off;
+  c->n_nbr = nbr_off;
+  apply_cells(c, c->opt.cell_div);
+  c->cfg = default_cfg(c);
+  c->cfg.cell_div = c->opt.cell_div;
+  if (c->opt.path == RE_PATH_BATCHED) {
+    int rc = check_cfg(c, c->cfg);
+    if (rc) return rc;
+  }
+  return allocate(c);
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+void re_default_opts(re_opts* o) {
+  if (!o) return;
+  o->dt = 0.005;
+  o->skin = 0.5;
+  o->tau_T = 0.5;
+  o->shift_energy = 1;
+  o->precision = RE_PREC_MIXED;
+  o->path = RE_PATH_BATCHED;
+  o->pair_parity = 0;
+  o->nx = 10;
+  o->nbr_capacity = 0;
+  o->cell_div = 0;
+  o->cluster = 0;
+  o->threads = 0;
+}
+
+int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
+              const re_opts* opt, re_ctx** out) {
+  g_create_error.clear();
+  if (!out) return fail(nullptr, RE_EINVAL, "out is NULL");
+  *out = nullptr;
+  re_opts o;
+  re_default_opts(&o);
+  if (opt) o = *opt;
+  if (n_rep < 1 || n_rep > 4096) return fail(nullptr, RE_EINVAL, "n_rep must be in [1, 4096]");
+  if (!temps) return fail(nullptr, RE_EINVAL, "temps is NULL");
+  int k = 1;
+  while (4 * k * k * k < N) ++k;
+  if (N < 4 || 4 * k * k * k != N) return fail(nullptr, RE_EINVAL, "N must be 4 k^3 (got %d)", N);
+  if (N > 65535) return fail(nullptr, RE_EINVAL, "N must be <= 65535 (got %d)", N);
+  if (!(L > 0) || !(rc > 0) || !(o.skin > 0) || !(o.dt > 0))
+    return fail(nullptr, RE_EINVAL, "L, rc, skin and dt must be positive");
+  if (rc + o.skin >= 0.5 * L)
+    return fail(nullptr, RE_EINVAL, "list radius rc + skin = %g must be below L/2 = %g", rc + o.skin,
+                0.5 * L);
+  if (o.precision != RE_PREC_FP64 && o.precision != RE_PREC_MIXED)
+    return fail(nullptr, RE_EINVAL, "unknown precision %d", o.precision);
+  if (o.path != RE_PATH_BATCHED && o.path != RE_PATH_PLAIN)
+    return fail(nullptr, RE_EINVAL, "unknown path %d", o.path);
+  if (o.path == RE_PATH_PLAIN) o.precision = RE_PREC_FP64;
+  if (o.nx < 0) return fail(nullptr, RE_EINVAL, "nx must be >= 0");
+  for (int i = 0; i < n_rep; ++i) {
+    if (!(temps[i] > 0)) return fail(nullptr, RE_EINVAL, "temperatures must be positive");
+    for (int j = 0; j < i; ++j)
+      if (temps[i] == temps[j]) return fail(nullptr, RE_EINVAL, "temperatures must be distinct");
+  }
+  re_ctx* c = new re_ctx();
+  c->opt = o;
+  cudaGetDevice(&c->device);
+  Ensemble e{N, n_rep, L, rc, std::vector<double>(temps, temps + n_rep), seed};
+  int rcode = build_context(c, {e}, nullptr);
+  if (rcode == RE_OK) {
+    cudaError_t ce = cudaMemcpyAsync(c->s.T, temps, sizeof(double) * n_rep,
+                                     cudaMemcpyHostToDevice, c->stream);
+    if (ce != cudaSuccess) rcode = cuda_fail(c, ce, "upload temps");
+  }
+  if (rcode == RE_OK) {
+    cudaError_t ce = re::launch_init_lattice(c->s, c->d_ens, c->d_rep, c->n_rep, 256, c->stream);
+    if (ce != cudaSuccess) rcode = cuda_fail(c, ce, "lattice init");
+  }
+  if (rcode == RE_OK) rcode = refresh(c);
+  if (rcode == RE_OK) rcode = status_check(c);
+  if (rcode != RE_OK) {
+    g_create_error = c->err;
+    re_destroy(c);
+    return rcode;
+  }
+  *out = c;
+  return RE_OK;
+}
+
+int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
+  g_create_error.clear();
+  if (!ctxs || n < 1 || !out) return fail(nullptr, RE_EINVAL, "bad arguments");
+  *out = nullptr;
+  std::vector<Ensemble> es;
+  std::vector<re_ctx*> src;
+  for (int i = 0; i < n; ++i) {
+    re_ctx* s = ctxs[i];
+    if (!s) return fail(nullptr, RE_EINVAL, "member %d is NULL", i);
+    if (s->ens.size() != 1) return fail(nullptr, RE_EINVAL, "members must be single ensembles");
+    if (s->opt.precision != ctxs[0]->opt.precision || s->opt.path != ctxs[0]->opt.path)
+      return fail(nullptr, RE_EINVAL, "members must share precision and path");
+    const EnsDev& e = s->ens[0];
+    es.push_back(Ensemble{e.N, e.R, e.L, e.rc, {}, e.seed});
+    src.push_back(s);
+    re_sync(s);
+  }
+  re_ctx* c = new re_ctx();
+  c->opt = ctxs[0]->opt;
+  // an explicit launch shape is kept only when every member asks for the same one
+  for (int i = 1; i < n; ++i) {
+    if (ctxs[i]->opt.cluster != c->opt.cluster) c->opt.cluster = 0;
+    if (ctxs[i]->opt.threads != c->opt.threads) c->opt.threads = 0;
+    if (ctxs[i]->opt.cell_div != c->opt.cell_div) c->opt.cell_div = 0;
+  }
+  cudaGetDevice(&c->device);
+  int rcode = build_context(c, es, &src);
+  // per-ensemble physics (skin, dt, tau, shift, parity) come from each member
+  if (rcode == RE_OK) {
+    for (int i = 0; i < n; ++i) {
+      const EnsDev& m = src[i]->ens[0];
+      EnsDev& e = c->ens[i];
+      e.skin = m.skin;
+      e.rlist = m.rlist;
+      e.dt = m.dt;
+      e.tau = m.tau;
+      e.shift = m.shift;
+      e.parity_mode = m.parity_mode;
+    }
+    apply_cells(c, c->opt.cell_div);
+    c->cfg = default_cfg(c);
+    if (c->opt.path == RE_PATH_BATCHED) rcode = check_cfg(c, c->cfg);
+    if (rcode == RE_OK) rcode = upload_tables(c);
+  }
+  // copy member states
+  for (int i = 0; i < n && rcode == RE_OK; ++i) {
+    re_ctx* s = src[i];
+    const int r0 = c->ens[i].rep_off;
+    const size_t a0 = (size_t)c->reps[r0].atom_off, A = (size_t)s->n_atoms;
+    const size_t R = (size_t)s->n_rep;
+    auto cp = [&](void* dst, const void* srcp, size_t bytes) {
+      cudaError_t e = cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      if (e != cudaSuccess && rcode == RE_OK) rcode = cuda_fail(c, e, "copy member state");
+    };
+    cp(c->s.qx + a0, s->s.qx, 8 * A);
+    cp(c->s.qy + a0, s->s.qy, 8 * A);
+    cp(c->s.qz + a0, s->s.qz, 8 * A);
+    cp(c->s.vx + a0, s->s.vx, 8 * A);
+    cp(c->s.vy + a0, s->s.vy, 8 * A);
+    cp(c->s.vz + a0, s->s.vz, 8 * A);
+    cp(c->s.fx + a0, s->s.fx, 8 * A);
+    cp(c->s.fy + a0, s->s.fy, 8 * A);
+    cp(c->s.fz + a0, s->s.fz, 8 * A);
+    cp(c->s.T + r0, s->s.T, 8 * R);
+    cp(c->s.U + r0, s->s.U, 8 * R);
+    cp(c->s.K + r0, s->s.K, 8 * R);
+    cp(c->s.econs + r0, s->s.econs, 8 * R);
+    cp(c->s.vscale + r0, s->s.vscale, 8 * R);
+    cp(c->s.step + r0, s->s.step, 8 * R);
+    cp(c->s.nreb + r0, s->s.nreb, 8 * R);
+    cp(c->s.status + r0, s->s.status, 4 * R);
+    cp(c->s.attempt + i, s->s.attempt, 8);
+    if (s->n_pairs > 0) {
+      cp(c->s.pair_att + c->ens[i].pair_off, s->s.pair_att, 8 * (size_t)s->n_pairs);
+      cp(c->s.pair_acc + c->ens[i].pair_off, s->s.pair_acc, 8 * (size_t)s->n_pairs);
+    }
+  }
+  if (rcode == RE_OK) {
+    cudaError_t ce = cudaMemsetAsync(c->s.valid, 0, sizeof(int32_t) * c->n_rep, c->stream);
+    if (ce != cudaSuccess) rcode = cuda_fail(c, ce, "memset");
+  }
+  if (rcode == RE_OK) rcode = refresh(c);
+  if (rcode == RE_OK) rcode = status_check(c);
+  if (rcode != RE_OK) {
+    g_create_error = c->err;
+    re_destroy(c);
+    return rcode;
+  }
+  *out = c;
+  return RE_OK;
+}
+
+int re_advance(re_ctx* c, const int32_t* steps) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (!steps) return launch_advance(c, c->d_budget_nx, nullptr);
+  for (int r = 0; r < c->n_rep; ++r)
+    if (steps[r] < 0) return fail(c, RE_EINVAL, "steps[%d] is negative", r);
+  if (c->opt.path == RE_PATH_PLAIN) return launch_advance(c, nullptr, steps);
+  // stage the budgets in a pinned ring slot, then copy asynchronously
+  const int slot = c->ring_pos;
+  c->ring_pos = (c->ring_pos + 1) % kRing;
+  RE_CUDA(c, cudaEventSynchronize(c->ring_ev[slot]), "ring wait");
+  int32_t* h = c->h_ring + (size_t)slot * c->n_rep;
+  std::memcpy(h, steps, sizeof(int32_t) * c->n_rep);
+  RE_CUDA(c, cudaMemcpyAsync(c->d_budget, h, sizeof(int32_t) * c->n_rep, cudaMemcpyHostToDevice,
+                             c->stream), "upload budgets");
+  RE_CUDA(c, cudaEventRecord(c->ring_ev[slot], c->stream), "ring record");
+  return launch_advance(c, c->d_budget, nullptr);
+}
+
+int re_exchange(re_ctx* c, int32_t* partner_out, uint8_t* accepted_out) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r, c->d_partner,
+                                      c->d_acc, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+  if (partner_out)
+    RE_CUDA(c, cudaMemcpyAsync(partner_out, c->d_partner, sizeof(int32_t) * c->n_rep,
+                               cudaMemcpyDeviceToHost, c->stream), "read partners");
+  if (accepted_out)
+    RE_CUDA(c, cudaMemcpyAsync(accepted_out, c->d_acc, c->n_rep, cudaMemcpyDeviceToHost,
+                               c->stream), "read accepted");
+  if (partner_out || accepted_out) RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  return RE_OK;
+}
+
+int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (n_cycles < 0) return fail(c, RE_EINVAL, "n_cycles must be >= 0");
+  if (n_cycles == 0) return RE_OK;
+  if (c->opt.path == RE_PATH_PLAIN) {
+    for (int k = 0; k < n_cycles; ++k) {
+      int rc = re_advance(c, steps ? steps + (size_t)k * c->n_rep : nullptr);
+      if (rc) return rc;
+      rc = re_exchange(c, nullptr, nullptr);
+      if (rc) return rc;
+    }
+    return RE_OK;
+  }
+  const int32_t* dbud = c->d_budget_nx;
+  size_t stride = 0;
+  if (steps) {
+    const size_t need = (size_t)n_cycles * c->n_rep;
+    for (size_t i = 0; i < need; ++i)
+      if (steps[i] < 0) return fail(c, RE_EINVAL, "negative step budget");
+    if (need > c->budget_run_cap) {
+      if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+      }
+      if (c->d_budget_run) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->d_budget_run);
+        auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)c->d_budget_run);
+        if (it != c->allocs.end()) c->allocs.erase(it);
+        c->d_budget_run = nullptr;
+      }
+      int rc = dalloc(c, &c->d_budget_run, need);
+      if (rc) return rc;
+      c->budget_run_cap = need;
+    }
+    RE_CUDA(c, cudaMemcpyAsync(c->d_budget_run, steps, sizeof(int32_t) * need,
+                               cudaMemcpyHostToDevice, c->stream), "upload budgets");
+    dbud = c->d_budget_run;
+    stride = (size_t)c->n_rep;
+  }
+  auto enqueue = [&]() -> int {
+    for (int k = 0; k < n_cycles; ++k) {
+      int rc = launch_advance(c, dbud + stride * k, nullptr);
+      if (rc) return rc;
+      cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
+                                          c->d_partner, c->d_acc, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+    }
+    return RE_OK;
+  };
+  if (!use_graph) return enqueue();
+  if (!c->graph || c->graph_cycles != n_cycles || c->graph_budget != dbud) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    RE_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int rc = RE_OK;
+    if (e == cudaSuccess) {
+      rc = enqueue();
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      if (rc == RE_OK && e2 != cudaSuccess) rc = cuda_fail(c, e2, "graph capture");
+    } else {
+      rc = cuda_fail(c, e, "begin capture");
+    }
+    c->stream = saved;
+    cudaStreamDestroy(cap);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->graph_cycles = n_cycles;
+    c->graph_budget = dbud;
+  }
+  RE_CUDA(c, cudaGraphLaunch(c->graph, c->stream), "graph launch");
+  return RE_OK;
+}
+
+int re_energies(re_ctx* c, double* U, double* K, double* H) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  int rc = status_check(c);
+  if (rc) return rc;
+  const size_t R = (size_t)c->n_rep;
+  std::vector<double> u(R), k(R), e(R);
+  RE_CUDA(c, cudaMemcpy(u.data(), c->s.U, 8 * R, cudaMemcpyDeviceToHost), "read U");
+  RE_CUDA(c, cudaMemcpy(k.data(), c->s.K, 8 * R, cudaMemcpyDeviceToHost), "read K");
+  RE_CUDA(c, cudaMemcpy(e.data(), c->s.econs, 8 * R, cudaMemcpyDeviceToHost), "read econs");
+  for (size_t r = 0; r < R; ++r) {
+    if (U) U[r] = u[r];
+    if (K) K[r] = k[r];
+    if (H) H[r] = u[r] + k[r] + e[r];
+  }
+  return RE_OK;
+}
+
+int re_temps(re_ctx* c, double* T) {
+  if (!c || !T) return fail(c, RE_EINVAL, "bad arguments");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  RE_CUDA(c, cudaMemcpy(T, c->s.T, sizeof(double) * c->n_rep, cudaMemcpyDeviceToHost), "read T");
+  return RE_OK;
+}
+
+int re_get_state(re_ctx* c, double* x, double* v) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  const size_t n3 = 3 * (size_t)c->n_atoms;
+  cudaError_t e = re::launch_apply_vscale(c->s, c->d_rep, c->d_ens, c->n_rep, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply velocity factors");
+  if (x) {
+    e = re::launch_export_state(c->s, c->d_ens, c->d_rep, c->n_rep, c->d_io, nullptr, nullptr,
+                                c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "export");
+    RE_CUDA(c, cudaMemcpyAsync(x, c->d_io, 8 * n3, cudaMemcpyDeviceToHost, c->stream), "read x");
+    RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  if (v) {
+    e = re::launch_export_state(c->s, c->d_ens, c->d_rep, c->n_rep, nullptr, c->d_io, nullptr,
+                                c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "export");
+    RE_CUDA(c, cudaMemcpyAsync(v, c->d_io, 8 * n3, cudaMemcpyDeviceToHost, c->stream), "read v");
+  }
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  return RE_OK;
+}
+
+int re_set_state(re_ctx* c, const double* x, const double* v) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  const size_t n3 = 3 * (size_t)c->n_atoms;
+  cudaError_t e = re::launch_apply_vscale(c->s, c->d_rep, c->d_ens, c->n_rep, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply velocity factors");
+  if (x) {
+    RE_CUDA(c, cudaMemcpyAsync(c->d_io, x, 8 * n3, cudaMemcpyHostToDevice, c->stream), "write x");
+    e = re::launch_import_state(c->s, c->d_ens, c->d_rep, c->n_rep, c->d_io, nullptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "import");
+    RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  if (v) {
+    RE_CUDA(c, cudaMemcpyAsync(c->d_io, v, 8 * n3, cudaMemcpyHostToDevice, c->stream), "write v");
+    e = re::launch_import_state(c->s, c->d_ens, c->d_rep, c->n_rep, nullptr, c->d_io, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "import");
+  }
+  int rc = refresh(c);
+  if (rc) return rc;
+  return status_check(c);
+}
+
+int re_forces(re_ctx* c, double* f) {
+  if (!c || !f) return fail(c, RE_EINVAL, "bad arguments");
+  int rc = status_check(c);
+  if (rc) return rc;
+  cudaError_t e = re::launch_export_state(c->s, c->d_ens, c->d_rep, c->n_rep, nullptr, nullptr,
+                                          c->d_io, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "export");
+  RE_CUDA(c, cudaMemcpyAsync(f, c->d_io, 8 * 3 * (size_t)c->n_atoms, cudaMemcpyDeviceToHost,
+                             c->stream), "read f");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  return RE_OK;
+}
+
+int re_counters(re_ctx* c, int64_t* steps, int64_t* rebuilds) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (steps)
+    RE_CUDA(c, cudaMemcpy(steps, c->s.step, 8 * (size_t)c->n_rep, cudaMemcpyDeviceToHost), "read");
+  if (rebuilds)
+    RE_CUDA(c, cudaMemcpy(rebuilds, c->s.nreb, 8 * (size_t)c->n_rep, cudaMemcpyDeviceToHost),
+            "read");
+  return RE_OK;
+}
+
+int re_accept_stats(re_ctx* c, int64_t* attempts, int64_t* accepts) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (c->n_pairs == 0) return RE_OK;
+  if (attempts)
+    RE_CUDA(c, cudaMemcpy(attempts, c->s.pair_att, 8 * (size_t)c->n_pairs, cudaMemcpyDeviceToHost),
+            "read");
+  if (accepts)
+    RE_CUDA(c, cudaMemcpy(accepts, c->s.pair_acc, 8 * (size_t)c->n_pairs, cudaMemcpyDeviceToHost),
+            "read");
+  return RE_OK;
+}
+
+int re_info(const re_ctx* c, int* n_rep, int64_t* n_atoms, int* n_ens, int* n_pairs) {
+  if (!c) return RE_EINVAL;
+  if (n_rep) *n_rep = c->n_rep;
+  if (n_atoms) *n_atoms = c->n_atoms;
+  if (n_ens) *n_ens = (int)c->ens.size();
+  if (n_pairs) *n_pairs = c->n_pairs;
+  return RE_OK;
+}
+
+int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div) {
+  if (!c) return RE_EINVAL;
+  if (cluster) *cluster = c->cfg.cluster;
+  if (threads) *threads = c->cfg.threads;
+  if (cell_div) *cell_div = c->ens.empty() ? 0 : c->ens[0].m;
+  return RE_OK;
+}
+
+int re_autotune(re_ctx* c, int steps) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (c->opt.path != RE_PATH_BATCHED) return RE_OK;
+  if (steps < 1) steps = 10;
+  int rc = status_check(c);
+  if (rc) return rc;
+  // snapshot everything a trial run changes
+  const size_t A = (size_t)c->n_atoms, R = (size_t)c->n_rep;
+  struct Buf {
+    void* dev;
+    size_t bytes;
+    void* save;
+  };
+  std::vector<Buf> bufs = {
+      {c->s.qx, 8 * A}, {c->s.qy, 8 * A}, {c->s.qz, 8 * A}, {c->s.vx, 8 * A},
+      {c->s.vy, 8 * A}, {c->s.vz, 8 * A}, {c->s.fx, 8 * A}, {c->s.fy, 8 * A},
+      {c->s.fz, 8 * A}, {c->s.U, 8 * R},  {c->s.K, 8 * R},  {c->s.econs, 8 * R},
+      {c->s.vscale, 8 * R}, {c->s.step, 8 * R}, {c->s.nreb, 8 * R}, {c->s.status, 4 * R}};
+  for (auto& b : bufs) {
+    b.save = nullptr;
+    cudaError_t e = cudaMalloc(&b.save, b.bytes);
+    if (e != cudaSuccess) {
+      for (auto& q : bufs)
+        if (q.save) cudaFree(q.save);
+      return cuda_fail(c, e, "autotune snapshot");
+    }
+    cudaMemcpyAsync(b.save, b.dev, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  std::vector<int32_t> bud(R, steps);
+  RE_CUDA(c, cudaMemcpyAsync(c->d_budget, bud.data(), 4 * R, cudaMemcpyHostToDevice, c->stream),
+          "upload");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const LaunchCfg keep = c->cfg;
+  const int keep_m = c->ens[0].m;
+  LaunchCfg best = keep;
+  int best_m = c->opt.cell_div;
+  float best_ms = 1e30f;
+  const int clusters[4] = {1, 2, 4, 8};
+  const int threads[4] = {128, 256, 384, 512};
+  for (int m = 0; m <= 3; ++m) {
+    if (c->opt.cell_div > 0 && m != c->opt.cell_div) continue;
+    apply_cells(c, m);
+    if (m > 0) {
+      bool any = false;
+      for (auto& e : c->ens) any |= (e.m == m);
+      if (!any) continue;
+    }
+    upload_tables(c);
+    for (int ci = 0; ci < 4; ++ci) {
+      if (c->opt.cluster > 0 && clusters[ci] != c->opt.cluster) continue;
+      for (int ti = 0; ti < 4; ++ti) {
+        if (c->opt.threads > 0 && threads[ti] != c->opt.threads) continue;
+        LaunchCfg k{clusters[ci], threads[ti], m};
+        if ((c->max_n + k.cluster - 1) / k.cluster < 32) continue;
+        if (check_cfg(c, k) != RE_OK) continue;
+        c->cfg = k;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          // restore, force a rebuild so every trial starts alike, then time
+          for (auto& b : bufs)
+            cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
+          cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
+          cudaEventRecord(e0, c->stream);
+          if (launch_advance(c, c->d_budget, nullptr) != RE_OK) break;
+          cudaEventRecord(e1, c->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) break;
+          float t = 0;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
+        }
+        cudaGetLastError();
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = k;
+          best_m = m;
+        }
+      }
+    }
+  }
+  c->cfg = best;
+  apply_cells(c, best_m);
+  (void)keep_m;
+  upload_tables(c);
+  for (auto& b : bufs) {
+    cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
+  cudaStreamSynchronize(c->stream);
+  for (auto& b : bufs) cudaFree(b.save);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  rc = refresh(c);
+  if (rc) return rc;
+  return status_check(c);
+}
+
+int re_set_stream(re_ctx* c, void* stream) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  c->stream = static_cast<cudaStream_t>(stream);
+  return RE_OK;
+}
+
+int re_sync(re_ctx* c) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  return status_check(c);
+}
+
+const char* re_last_error(const re_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+void re_destroy(re_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_ring) cudaFreeHost(c->h_ring);
+  for (int k = 0; k < kRing; ++k)
+    if (c->ring_ev[k]) cudaEventDestroy(c->ring_ev[k]);
+  delete c;
+}
+
+int re_exchange_device(int R, const double* T, const double* U, uint64_t seed, int64_t attempt,
+                       int parity_mode, double* T_out, int32_t* partner, uint8_t* accepted,
+                       double* vscale, void* stream) {
+  g_create_error.clear();
+  if (R < 1 || R > 4096) return fail(nullptr, RE_EINVAL, "R must be in [1, 4096]");
+  if (!T || !U || !T_out || !partner || !accepted || !vscale)
+    return fail(nullptr, RE_EINVAL, "NULL device pointer");
+  if (parity_mode != 0 && parity_mode != 1) return fail(nullptr, RE_EINVAL, "parity_mode 0 or 1");
+  cudaError_t e = re::launch_exchange_raw(R, T, U, seed, attempt, parity_mode, T_out, partner,
+                                          accepted, vscale, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "exchange launch");
+  return RE_OK;
+}
+
+int re_lj_forces_device(int N, double L, double rc, int shift, int precision, const double* x,
+                        double* f, double* U, void* stream) {
+  g_create_error.clear();
+  if (N < 2 || N > 65535) return fail(nullptr, RE_EINVAL, "N must be in [2, 65535]");
+  if (!x || !f || !U) return fail(nullptr, RE_EINVAL, "NULL device pointer");
+  if (!(L > 0) || !(rc > 0) || rc + 0.5 >= 0.5 * L)
+    return fail(nullptr, RE_EINVAL, "need rc + 0.5 < L/2");
+  if (precision != RE_PREC_FP64 && precision != RE_PREC_MIXED)
+    return fail(nullptr, RE_EINVAL, "unknown precision");
+  // A one-replica context without lattice set-up: import x, prologue, export f.
+  re_ctx* c = new re_ctx();
+  re_default_opts(&c->opt);
+  c->opt.precision = precision;
+  c->opt.shift_energy = shift;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  Ensemble e{N, 1, L, rc, {1.0}, 0};
+  int rcode = build_context(c, {e}, nullptr);
+  auto bail = [&](int code) {
+    g_create_error = c->err;
+    re_destroy(c);
+    return code;
+  };
+  if (rcode) return bail(rcode);
+  const double one = 1.0;
+  int32_t zero = 0;
+  cudaError_t ce;
+  if ((ce = cudaMemcpyAsync(c->s.T, &one, 8, cudaMemcpyHostToDevice, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.vx, 0, 8 * (size_t)N, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.vy, 0, 8 * (size_t)N, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.vz, 0, 8 * (size_t)N, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.econs, 0, 8, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.step, 0, 8, c->stream)) ||
+      (ce = cudaMemsetAsync(c->s.nreb, 0, 8, c->stream)) ||
+      (ce = cudaMemcpyAsync(c->s.status, &zero, 4, cudaMemcpyHostToDevice, c->stream)))
+    return bail(cuda_fail(c, ce, "set-up"));
+  ce = re::launch_import_state(c->s, c->d_ens, c->d_rep, 1, x, nullptr, c->stream);
+  if (ce != cudaSuccess) return bail(cuda_fail(c, ce, "import"));
+  rcode = refresh(c);
+  if (rcode == RE_OK) rcode = status_check(c);
+  if (rcode) return bail(rcode);
+  ce = re::launch_export_state(c->s, c->d_ens, c->d_rep, 1, nullptr, nullptr, f, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(U, c->s.U, 8, cudaMemcpyDeviceToDevice, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) return bail(cuda_fail(c, ce, "export"));
+  re_destroy(c);
+  return RE_OK;
+}
+
+}  // extern "C"

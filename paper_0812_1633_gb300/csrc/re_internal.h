@@ -1,0 +1,82 @@
+// re_internal.h -- data layout shared by the host side (re_capi.cu) and the
+// kernels (re_kernels.cu) of the replica-exchange library.  Not installed.
+//
+// Device memory of a context (all replicas of all ensembles, SoA):
+//   qx,qy,qz  uint64 [atoms]   positions, fixed point x/L * 2^64 (wrapping)
+//   vx,vy,vz  double [atoms]   velocities
+//   fx,fy,fz  double [atoms]   forces at the current positions
+//   rx,ry,rz  uint32 [atoms]   top 32 bits of the positions at the last rebuild
+//   ncnt      int32  [atoms]   neighbour count of each atom
+//   nbr       uint16 [sum over replicas of cap * N]  neighbour indices, per
+//             replica in blocks of four: entry k of atom i at
+//             ((k / 4) * N + i) * 4 + k % 4  (local atom indices)
+//   per replica: T, U, K, econs, vscale (pending velocity factor), step,
+//             nreb, status, valid
+//   per ensemble: attempt counter; per sorted pair position: attempts, accepts
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace re {
+
+enum StatusBits : int { kStOverflow = 1, kStNumeric = 2, kStRngCap = 4 };
+
+struct EnsDev {
+  int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
+  int nc, m;                    // list cells per side (0: all pairs), reach in cells
+  int cap;                      // neighbour capacity per atom (multiple of 4)
+  int shift, parity_mode, pad_;
+  double L, rc, rlist, skin, dt, tau;
+  uint64_t seed;
+};
+
+struct RepDev {
+  int ens, id, atom_off, pad_;
+  int64_t nbr_off;
+};
+
+struct StateDev {
+  uint64_t *qx, *qy, *qz;
+  double *vx, *vy, *vz, *fx, *fy, *fz;
+  uint32_t *rx, *ry, *rz;
+  int32_t* ncnt;
+  uint16_t* nbr;
+  double *T, *U, *K, *econs, *vscale;
+  int64_t *step, *nreb;
+  int32_t *status, *valid;
+  int64_t* attempt;                  // per ensemble
+  int64_t *pair_att, *pair_acc;      // per ensemble pair position
+  double* red;                       // plain path: per replica reduction scratch
+  uint32_t* dmax;                    // plain path: per replica max displacement^2 (float bits)
+};
+
+struct LaunchCfg {
+  int cluster, threads, cell_div;
+};
+
+// Host-side launchers (re_kernels.cu).  All return the launch status.
+cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                int n_rep, int max_threads, cudaStream_t st);
+size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64);
+cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                           const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
+                           const LaunchCfg& cfg, int max_n, int max_ncell, cudaStream_t st);
+cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,
+                                 const EnsDev* d_ens, const RepDev* d_rep, int steps,
+                                 int max_ncell, cudaStream_t st, int refresh);
+cudaError_t launch_exchange(const StateDev& s, const EnsDev* d_ens, int n_ens, int max_r,
+                            int32_t* d_partner, uint8_t* d_acc, cudaStream_t st);
+cudaError_t launch_apply_vscale(const StateDev& s, const RepDev* d_rep, const EnsDev* d_ens,
+                                int n_rep, cudaStream_t st);
+cudaError_t launch_export_state(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                int n_rep, double* d_x, double* d_v, double* d_f,
+                                cudaStream_t st);
+cudaError_t launch_import_state(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                int n_rep, const double* d_x, const double* d_v,
+                                cudaStream_t st);
+cudaError_t launch_exchange_raw(int R, const double* T, const double* U, uint64_t seed,
+                                int64_t attempt, int parity_mode, double* T_out,
+                                int32_t* partner, uint8_t* accepted, double* vscale,
+                                cudaStream_t st);
+
+}  // namespace re
