@@ -269,8 +269,8 @@ def run_gpu(args, cfg):
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
     if args.launch:
-        cl, th, cd = (int(v) for v in args.launch.split(","))
-        members_kw = dict(cluster=cl, threads=th, cell_div=cd)
+        cl, at, cd = (int(v) for v in args.launch.split(","))
+        members_kw = dict(cluster=cl, atom_threads=at, cell_div=cd)
         ctx.close()
         members = []
         for i, (N, R, t0, t1) in enumerate(ens_spec):
@@ -284,7 +284,7 @@ def run_gpu(args, cfg):
         ctx.set_stream(stream)
         tuned = ctx.config()
     else:
-        tuned = ctx.autotune(steps=max(5, min(20, nx if nx else 20)))
+        tuned = ctx.autotune(steps=40)
     Rtot = ctx.n_rep
     W, K = args.warmup, args.steps
     budgets = make_budgets(cfg, Rtot, W + K, 7 + rank)
@@ -422,7 +422,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--launch", default=None,
-                    help="fixed launch shape 'cluster,threads,cell_div' instead of the autotuner")
+                    help="fixed launch shape 'cluster,atom_threads,cell_div' instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -71,10 +71,10 @@ typedef struct re_opts {
   int path;         /* RE_PATH_BATCHED (default) or RE_PATH_PLAIN                     */
   int pair_parity;  /* 0 (default): first pair offset alternates 0,1; 1: random      */
   int nx;           /* steps per replica used by re_advance(c, NULL); default 10      */
-  int nbr_capacity; /* neighbours per atom (multiple of 4); 0: from the density        */
+  int nbr_capacity; /* neighbours per atom; 0: from the density with a 6-sigma margin */
   int cell_div;     /* list cells per list radius (1..3); 0: automatic               */
   int cluster;      /* CTAs cooperating on one replica (1, 2, 4, 8); 0: automatic     */
-  int threads;      /* threads per CTA (64..512, multiple of 32); 0: automatic        */
+  int atom_threads; /* threads sharing one atom's neighbour list (1, 2, 4, 8); 0: auto */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -136,9 +136,10 @@ int re_accept_stats(re_ctx *c, int64_t *attempts, int64_t *accepts);
 /* Shape of the context: replicas, atoms of all replicas, ensembles, pair
  * stats entries (any may be NULL). */
 int re_info(const re_ctx *c, int *n_rep, int64_t *n_atoms, int *n_ens, int *n_pairs);
-/* Launch configuration in use: cluster, threads, cell_div (any may be NULL). */
-int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div);
-/* Times candidate launch configurations (cluster, threads, cell_div) over
+/* Launch configuration in use: CTAs per replica, threads per CTA, list cells
+ * per list radius, threads per atom (any may be NULL). */
+int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads);
+/* Times candidate launch configurations (cluster, atom_threads, cell_div) over
  * `steps` steps each on a copy of the state and keeps the fastest; the state
  * is restored afterwards. */
 int re_autotune(re_ctx *c, int steps);

@@ -33,7 +33,7 @@ class _Opts(C.Structure):
     _fields_ = [("dt", C.c_double), ("skin", C.c_double), ("tau_T", C.c_double),
                 ("shift_energy", C.c_int), ("precision", C.c_int), ("path", C.c_int),
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
-                ("cell_div", C.c_int), ("cluster", C.c_int), ("threads", C.c_int)]
+                ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int)]
 
 
 _lib = None
@@ -65,7 +65,8 @@ def lib():
         L.re_counters.argtypes = [vp, i64p, i64p]
         L.re_accept_stats.argtypes = [vp, i64p, i64p]
         L.re_info.argtypes = [vp, C.POINTER(C.c_int), i64p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
-        L.re_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.re_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int)]
         L.re_autotune.argtypes = [vp, C.c_int]
         L.re_set_stream.argtypes = [vp, vp]
         L.re_sync.argtypes = [vp]
@@ -103,7 +104,7 @@ class Context:
 
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
-                 cell_div=0, cluster=0, threads=0, _handle=None):
+                 cell_div=0, cluster=0, atom_threads=0, _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -114,7 +115,7 @@ class Context:
             o.shift_energy = 1 if shift else 0
             o.precision, o.path = PREC[precision], PATH[path]
             o.pair_parity, o.nx, o.nbr_capacity = pair_parity, nx, nbr_capacity
-            o.cell_div, o.cluster, o.threads = cell_div, cluster, threads
+            o.cell_div, o.cluster, o.atom_threads = cell_div, cluster, atom_threads
             t = np.ascontiguousarray(temps, dtype=np.float64)
             _check(lib().re_create(int(N), float(L), float(rc), len(t), _p(t, C.c_double),
                                    int(seed) & (2**64 - 1), C.byref(o), C.byref(self._h)))
@@ -219,9 +220,10 @@ class Context:
         return a[:self.n_pairs], b[:self.n_pairs]
 
     def config(self):
-        cl, th, cd = C.c_int(), C.c_int(), C.c_int()
-        lib().re_config(self._h, C.byref(cl), C.byref(th), C.byref(cd))
-        return {"cluster": cl.value, "threads": th.value, "cell_div": cd.value}
+        cl, th, cd, at = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib().re_config(self._h, C.byref(cl), C.byref(th), C.byref(cd), C.byref(at))
+        return {"cluster": cl.value, "threads": th.value, "cell_div": cd.value,
+                "atom_threads": at.value}
 
     def autotune(self, steps=10):
         _check(lib().re_autotune(self._h, int(steps)), self._h)

@@ -19,6 +19,54 @@ using re::EnsDev;
 using re::LaunchCfg;
 using re::RepDev;
 using re::StateDev;
+using re::choose_cells;
+using re::set_capacity;
+
+namespace re {
+
+// List cells: nc = floor(L / (rlist / m)) cells per side scanned over a
+// (2m + 1)^3 neighbourhood; cells only pay when 2m + 1 < nc.  m is chosen
+// to minimise candidates per atom plus a per-cell visiting cost.
+void choose_cells(double L, double rlist, int N, int want_m, int* nc_out, int* m_out) {
+  double best = (double)N;  // all pairs
+  int bnc = 0, bm = 0;
+  for (int m = 1; m <= 3; ++m) {
+    if (want_m > 0 && m != want_m) continue;
+    const int nc = (int)std::floor(L / (rlist / m));
+    if (nc < 2 * m + 2 || nc * nc * nc > 65535) continue;
+    const double span = 2.0 * m + 1.0;
+    const double cost = N * span * span * span / ((double)nc * nc * nc) + 4.0 * span * span * span;
+    if (cost < best) {
+      best = cost;
+      bnc = nc;
+      bm = m;
+    }
+  }
+  *nc_out = bnc;
+  *m_out = bm;
+}
+
+// Neighbour capacity of one of P sub-lists: the uniform-density count m
+// within rlist split P ways, plus six standard deviations of a Poisson count
+// and 4, rounded up to a whole block of four (at most one entry per atom).
+// A user capacity c (per atom) gives ceil(c / P) per sub-list.
+void set_capacity(EnsDev& e, int user_cap) {
+  const double rho = e.N / (e.L * e.L * e.L);
+  const double m = rho * 4.0 / 3.0 * M_PI * e.rlist * e.rlist * e.rlist;
+  const int pv[4] = {1, 2, 4, 8};
+  e.cap = 0;
+  for (int k = 0; k < 4; ++k) {
+    const double mp = m / pv[k];
+    int cs = user_cap > 0 ? (user_cap + pv[k] - 1) / pv[k]
+                          : (int)std::ceil(mp + 6.0 * std::sqrt(mp) + 4.0);
+    cs = std::min(cs, e.N + 3);
+    cs = std::max(4, (cs + 3) / 4 * 4);
+    e.capsub[k] = cs;
+    e.cap = std::max(e.cap, cs * pv[k]);
+  }
+}
+
+}  // namespace re
 
 namespace {
 
@@ -42,7 +90,7 @@ struct re_ctx {
   int n_rep = 0, n_pairs = 0;
   int64_t n_atoms = 0, n_nbr = 0;
   int max_n = 0, max_r = 0, max_ncell = 0;
-  LaunchCfg cfg{1, 256, 0};
+  LaunchCfg cfg{1, 256, 0, 1};
   cudaStream_t stream = nullptr;
   int device = 0;
   StateDev s{};
@@ -105,35 +153,9 @@ int dalloc(re_ctx* c, T** p, size_t n) {
   return RE_OK;
 }
 
-// List cells: nc = floor(L / (rlist / m)) cells per side scanned over a
-// (2m + 1)^3 neighbourhood; cells only pay when 2m + 1 < nc.  m is chosen
-// to minimise candidates per atom plus a per-cell visiting cost.
-void choose_cells(double L, double rlist, int N, int want_m, int* nc_out, int* m_out) {
-  double best = (double)N;  // all pairs
-  int bnc = 0, bm = 0;
-  for (int m = 1; m <= 3; ++m) {
-    if (want_m > 0 && m != want_m) continue;
-    const int nc = (int)std::floor(L / (rlist / m));
-    if (nc < 2 * m + 2 || nc * nc * nc > 65535) continue;
-    const double span = 2.0 * m + 1.0;
-    const double cost = N * span * span * span / ((double)nc * nc * nc) + 4.0 * span * span * span;
-    if (cost < best) {
-      best = cost;
-      bnc = nc;
-      bm = m;
-    }
-  }
-  *nc_out = bnc;
-  *m_out = bm;
-}
-
-int default_capacity(int N, double L, double rlist) {
-  const double rho = N / (L * L * L);
-  const double mean = rho * 4.0 / 3.0 * M_PI * rlist * rlist * rlist;
-  int cap = (int)std::ceil(1.5 * mean + 16.0);
-  cap = (cap + 3) / 4 * 4;
-  cap = std::min(cap, ((N - 1) + 3) / 4 * 4);
-  return std::max(cap, 4);
+int threads_for(int max_n, int cluster, int atom_threads) {
+  const int per = (max_n + cluster - 1) / cluster;
+  return std::max(32, (atom_threads * per + 31) / 32 * 32);
 }
 
 int sm_count() {
@@ -143,23 +165,25 @@ int sm_count() {
   return n > 0 ? n : 148;
 }
 
+// Default launch shape: enough CTAs per replica to cover the SMs in about one
+// wave, then as many threads per atom as fit in one CTA (at most 4).
 LaunchCfg default_cfg(const re_ctx* c) {
   LaunchCfg k{};
   const int sms = sm_count();
   int cl = c->opt.cluster;
   if (cl <= 0) {
     cl = 1;
-    while (cl < 8 && c->n_rep * cl * 2 <= sms * 2 && c->n_rep * (cl * 2) <= sms + sms / 4 &&
-           (c->max_n + cl * 2 - 1) / (cl * 2) >= 64)
+    while (cl < 8 && c->n_rep * cl < (sms * 4) / 5 && (c->max_n + 2 * cl - 1) / (2 * cl) >= 32)
       cl *= 2;
   }
-  int th = c->opt.threads;
-  if (th <= 0) {
-    const int per = (c->max_n + cl - 1) / cl;
-    th = std::min(512, std::max(64, (per + 31) / 32 * 32));
+  int p = c->opt.atom_threads;
+  if (p <= 0) {
+    p = 4;
+    while (p > 1 && threads_for(c->max_n, cl, p) > 1024) p /= 2;
   }
   k.cluster = cl;
-  k.threads = th;
+  k.atom_threads = p;
+  k.threads = threads_for(c->max_n, cl, p);
   k.cell_div = 0;
   return k;
 }
@@ -181,7 +205,7 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &s.vx, A)) || (rc = dalloc(c, &s.vy, A)) || (rc = dalloc(c, &s.vz, A)) ||
       (rc = dalloc(c, &s.fx, A)) || (rc = dalloc(c, &s.fy, A)) || (rc = dalloc(c, &s.fz, A)) ||
       (rc = dalloc(c, &s.rx, A)) || (rc = dalloc(c, &s.ry, A)) || (rc = dalloc(c, &s.rz, A)) ||
-      (rc = dalloc(c, &s.ncnt, A)) || (rc = dalloc(c, &s.nbr, (size_t)c->n_nbr)) ||
+      (rc = dalloc(c, &s.ncnt, 8 * A)) || (rc = dalloc(c, &s.nbr, (size_t)c->n_nbr)) ||
       (rc = dalloc(c, &s.T, R)) || (rc = dalloc(c, &s.U, R)) || (rc = dalloc(c, &s.K, R)) ||
       (rc = dalloc(c, &s.econs, R)) || (rc = dalloc(c, &s.vscale, R)) ||
       (rc = dalloc(c, &s.step, R)) || (rc = dalloc(c, &s.nreb, R)) ||
@@ -195,7 +219,7 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &c->d_acc, R)) || (rc = dalloc(c, &c->d_io, 3 * A)))
     return rc;
   RE_CUDA(c, cudaMemsetAsync(s.nbr, 0, sizeof(uint16_t) * (size_t)c->n_nbr, c->stream), "memset");
-  RE_CUDA(c, cudaMemsetAsync(s.ncnt, 0, sizeof(int32_t) * A, c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(s.ncnt, 0, sizeof(int32_t) * 8 * A, c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.attempt, 0, sizeof(int64_t) * E, c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.pair_att, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.pair_acc, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
@@ -230,8 +254,11 @@ void apply_cells(re_ctx* c, int want_m) {
 int check_cfg(re_ctx* c, const LaunchCfg& k) {
   if (k.cluster != 1 && k.cluster != 2 && k.cluster != 4 && k.cluster != 8)
     return fail(c, RE_EINVAL, "cluster must be 1, 2, 4 or 8 (got %d)", k.cluster);
-  if (k.threads < 64 || k.threads > 512 || k.threads % 32)
-    return fail(c, RE_EINVAL, "threads must be a multiple of 32 in [64, 512] (got %d)", k.threads);
+  if (k.atom_threads != 1 && k.atom_threads != 2 && k.atom_threads != 4 && k.atom_threads != 8)
+    return fail(c, RE_EINVAL, "atom_threads must be 1, 2, 4 or 8 (got %d)", k.atom_threads);
+  if (k.threads < 32 || k.threads > 1024 || k.threads % 32)
+    return fail(c, RE_EINVAL, "%d atoms per CTA x %d threads per atom exceed 1024 threads; "
+                "use more CTAs per replica", (c->max_n + k.cluster - 1) / k.cluster, k.atom_threads);
   const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
                                              c->opt.precision == RE_PREC_FP64);
   int dev = 0, maxsm = 0;
@@ -283,8 +310,8 @@ int status_check(re_ctx* c) {
                         cudaMemcpyDeviceToHost), "read status");
   for (int r = 0; r < c->n_rep; ++r) {
     if (st[r] & re::kStOverflow)
-      return fail(c, RE_EOVERFLOW, "replica %d: neighbour list capacity %d exceeded", r,
-                  c->ens[c->reps[r].ens].cap);
+      return fail(c, RE_EOVERFLOW, "replica %d: neighbour list capacity exceeded (%d per atom; "
+                  "raise nbr_capacity)", r, c->ens[c->reps[r].ens].cap);
     if (st[r] & (re::kStNumeric | re::kStRngCap))
       return fail(c, RE_ENUMERIC, "replica %d: non-finite energy or thermostat draw", r);
   }
@@ -310,9 +337,11 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
     e.shift = c->opt.shift_energy ? 1 : 0;
     e.parity_mode = c->opt.pair_parity;
     e.seed = s.seed;
-    e.cap = c->opt.nbr_capacity > 0 ? (c->opt.nbr_capacity + 3) / 4 * 4
-                                    : default_capacity(s.N, s.L, e.rlist);
-    if (src) e.cap = (*src)[k]->ens[0].cap;
+    set_capacity(e, c->opt.nbr_capacity);
+    if (src) {
+      e.cap = (*src)[k]->ens[0].cap;
+      for (int q = 0; q < 4; ++q) e.capsub[q] = (*src)[k]->ens[0].capsub[q];
+    }
     c->ens.push_back(e);
     for (int r = 0; r < s.R; ++r) {
       RepDev rd{};
@@ -362,7 +391,7 @@ void re_default_opts(re_opts* o) {
   o->nbr_capacity = 0;
   o->cell_div = 0;
   o->cluster = 0;
-  o->threads = 0;
+  o->atom_threads = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -442,7 +471,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
   // an explicit launch shape is kept only when every member asks for the same one
   for (int i = 1; i < n; ++i) {
     if (ctxs[i]->opt.cluster != c->opt.cluster) c->opt.cluster = 0;
-    if (ctxs[i]->opt.threads != c->opt.threads) c->opt.threads = 0;
+    if (ctxs[i]->opt.atom_threads != c->opt.atom_threads) c->opt.atom_threads = 0;
     if (ctxs[i]->opt.cell_div != c->opt.cell_div) c->opt.cell_div = 0;
   }
   cudaGetDevice(&c->device);
@@ -744,10 +773,11 @@ int re_info(const re_ctx* c, int* n_rep, int64_t* n_atoms, int* n_ens, int* n_pa
   return RE_OK;
 }
 
-int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div) {
+int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div, int* atom_threads) {
   if (!c) return RE_EINVAL;
   if (cluster) *cluster = c->cfg.cluster;
   if (threads) *threads = c->cfg.threads;
+  if (atom_threads) *atom_threads = c->cfg.atom_threads;
   if (cell_div) *cell_div = c->ens.empty() ? 0 : c->ens[0].m;
   return RE_OK;
 }
@@ -755,7 +785,8 @@ int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div) {
 int re_autotune(re_ctx* c, int steps) {
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (c->opt.path != RE_PATH_BATCHED) return RE_OK;
-  if (steps < 1) steps = 10;
+  // each trial starts with a full list build; enough steps that it does not dominate
+  steps = std::max(steps, 40);
   int rc = status_check(c);
   if (rc) return rc;
   // snapshot everything a trial run changes
@@ -792,7 +823,7 @@ int re_autotune(re_ctx* c, int steps) {
   int best_m = c->opt.cell_div;
   float best_ms = 1e30f;
   const int clusters[4] = {1, 2, 4, 8};
-  const int threads[4] = {128, 256, 384, 512};
+  const int pvals[4] = {1, 2, 4, 8};
   for (int m = 0; m <= 3; ++m) {
     if (c->opt.cell_div > 0 && m != c->opt.cell_div) continue;
     apply_cells(c, m);
@@ -804,10 +835,10 @@ int re_autotune(re_ctx* c, int steps) {
     upload_tables(c);
     for (int ci = 0; ci < 4; ++ci) {
       if (c->opt.cluster > 0 && clusters[ci] != c->opt.cluster) continue;
-      for (int ti = 0; ti < 4; ++ti) {
-        if (c->opt.threads > 0 && threads[ti] != c->opt.threads) continue;
-        LaunchCfg k{clusters[ci], threads[ti], m};
-        if ((c->max_n + k.cluster - 1) / k.cluster < 32) continue;
+      for (int pi = 0; pi < 4; ++pi) {
+        if (c->opt.atom_threads > 0 && pvals[pi] != c->opt.atom_threads) continue;
+        LaunchCfg k{clusters[ci], threads_for(c->max_n, clusters[ci], pvals[pi]), m, pvals[pi]};
+        if ((c->max_n + k.cluster - 1) / k.cluster < 16) continue;
         if (check_cfg(c, k) != RE_OK) continue;
         c->cfg = k;
         float ms = 1e30f;
@@ -825,6 +856,13 @@ int re_autotune(re_ctx* c, int steps) {
           ms = std::min(ms, t);
         }
         cudaGetLastError();
+        {
+          // a trial that overflowed or failed stopped early: never pick it
+          std::vector<int32_t> st(R);
+          cudaMemcpy(st.data(), c->s.status, 4 * R, cudaMemcpyDeviceToHost);
+          for (size_t r = 0; r < R; ++r)
+            if (st[r]) ms = 1e30f;
+        }
         if (ms < best_ms) {
           best_ms = ms;
           best = k;

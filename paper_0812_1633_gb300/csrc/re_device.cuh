@@ -93,6 +93,36 @@ __device__ inline double2 svr_noise(int nf, uint64_t seed, uint64_t stream, uint
   return make_double2(r1, s);
 }
 
+// The same draws in FP32 (mixed path): the top 24 bits of the same Philox
+// words, Box-Muller and Marsaglia-Tsang in single precision.
+__device__ __forceinline__ float to_unit_f(uint64_t w) { return (float)(w >> 40) * 5.9604644775390625e-08f; }
+
+__device__ inline float2 svr_noise_f32(int nf, uint64_t seed, uint64_t stream, uint64_t step,
+                                       int* capped) {
+  const U64x4 o = philox4x64_10(U64x4{step, kTagSvrR1, 0ull, 0ull}, seed, stream);
+  float s0, c0;
+  sincospif(2.0f * to_unit_f(o.b), &s0, &c0);
+  const float r1 = sqrtf(-2.0f * logf(1.0f - to_unit_f(o.a))) * c0;
+  const float a = 0.5f * (float)(nf - 1);
+  const float d = a - 1.0f / 3.0f;
+  const float c = rsqrtf(9.0f * d);
+  for (int t = 0; t < 256; ++t) {
+    const U64x4 g = philox4x64_10(U64x4{step, kTagSvrGamma, (uint64_t)t, 0ull}, seed, stream);
+    float sn, cs;
+    sincospif(2.0f * to_unit_f(g.b), &sn, &cs);
+    const float x = sqrtf(-2.0f * logf(1.0f - to_unit_f(g.a))) * cs;
+    const float w = 1.0f + c * x;
+    if (w <= 0.0f) continue;
+    const float v = w * w * w;
+    const float u = to_unit_f(g.c);
+    const float x2 = x * x;
+    if (u < 1.0f - 0.0331f * x2 * x2 || logf(u) < 0.5f * x2 + d * (1.0f - v + logf(v)))
+      return make_float2(r1, 2.0f * d * v);
+  }
+  *capped = 1;
+  return make_float2(r1, 2.0f * a);
+}
+
 // Stochastic velocity rescaling over one step: the new kinetic energy is
 //   K' = c K + (1 - c) Kbar (R1^2 + S)/Nf + 2 R1 sqrt(c (1 - c) Kbar K / Nf)
 // (c = exp(-dt/tau), Kbar = Nf T/2) and velocities scale by
@@ -131,6 +161,23 @@ __device__ __forceinline__ float i32_to_f32_split(int v) {
   const float hi = __int_as_float(0x4B400000 + (v >> 16)) - 12582912.0f;       // v >> 16 in [-2^15, 2^15)
   const float lo = __int_as_float(0x4B000000 | (v & 0xFFFF)) - 8388608.0f;     // low 16 bits
   return fmaf(hi, 65536.0f, lo);
+}
+
+// 64-bit integer <-> float conversions through two 32-bit conversions (the
+// 64-bit forms run on the FP64 unit, about 2 per clock per SM on this GPU;
+// the 32-bit forms run at more than 50 per clock).
+// nearest int64 to y, |y| < 2^62 (within one unit)
+__device__ __forceinline__ long long f2ll_split(float y) {
+  const int hi = __float2int_rn(y * 2.3283064365386963e-10f);  // y / 2^32
+  const float rem = fmaf((float)hi, -4294967296.0f, y);        // exact
+  const int lo = __float2int_rn(rem);
+  return ((long long)hi << 32) + (long long)lo;
+}
+// float nearest to v (one extra rounding of the low word, below 2^-24 relative)
+__device__ __forceinline__ float ll2f_split(long long v) {
+  const int hi = (int)(v >> 32);
+  const unsigned lo = (unsigned)(v & 0xFFFFFFFFll);
+  return fmaf((float)hi, 4294967296.0f, (float)lo);
 }
 
 // ------------------------------------------------------------- reductions

@@ -6,10 +6,11 @@
 //   vx,vy,vz  double [atoms]   velocities
 //   fx,fy,fz  double [atoms]   forces at the current positions
 //   rx,ry,rz  uint32 [atoms]   top 32 bits of the positions at the last rebuild
-//   ncnt      int32  [atoms]   neighbour count of each atom
-//   nbr       uint16 [sum over replicas of cap * N]  neighbour indices, per
-//             replica in blocks of four: entry k of atom i at
-//             ((k / 4) * N + i) * 4 + k % 4  (local atom indices)
+//   ncnt      int32  [8 * atoms] neighbour count of each (atom, lane) sub-list
+//   nbr       uint16 [sum over replicas of cap * N]  neighbour indices (local
+//             atom indices).  With P threads per atom each atom's list is split
+//             into P sub-lists of cap/P entries; entry k of sub-list (i, q) at
+//             ((k / 4) * N * P + i * P + q) * 4 + k % 4 (P = 1 on the plain path)
 //   per replica: T, U, K, econs, vscale (pending velocity factor), step,
 //             nreb, status, valid
 //   per ensemble: attempt counter; per sorted pair position: attempts, accepts
@@ -24,7 +25,8 @@ enum StatusBits : int { kStOverflow = 1, kStNumeric = 2, kStRngCap = 4 };
 struct EnsDev {
   int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
   int nc, m;                    // list cells per side (0: all pairs), reach in cells
-  int cap;                      // neighbour capacity per atom (multiple of 4)
+  int cap;                      // neighbour entries per atom: max over P of P * capsub[P]
+  int capsub[4];                // sub-list capacity (multiple of 4) for P = 1, 2, 4, 8
   int shift, parity_mode, pad_;
   double L, rc, rlist, skin, dt, tau;
   uint64_t seed;
@@ -51,8 +53,13 @@ struct StateDev {
 };
 
 struct LaunchCfg {
-  int cluster, threads, cell_div;
+  int cluster, threads, cell_div, atom_threads;  // CTAs per replica, threads per CTA,
+                                                 // list cells per list radius, threads per atom
 };
+
+// Host helpers (re_capi.cu): list cells of an ensemble and neighbour capacities.
+void choose_cells(double L, double rlist, int N, int want_m, int* nc_out, int* m_out);
+void set_capacity(EnsDev& e, int user_cap);
 
 // Host-side launchers (re_kernels.cu).  All return the launch status.
 cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,

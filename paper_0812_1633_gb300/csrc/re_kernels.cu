@@ -17,6 +17,8 @@
 //                      replica's uniform, swap T, rescale velocities.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "re_device.cuh"
 #include "re_internal.h"
 
@@ -29,6 +31,8 @@ namespace {
 constexpr int kMaxCluster = 8;
 constexpr int kMaxWarps = 32;
 constexpr int kPlainRed = 1024;  // per-replica reduction slots of the plain path
+constexpr int kNoiseChunk = 64;  // thermostat records prepared at a time (double buffered)
+constexpr int kSvrStepBytes = 40;  // sizeof(SvrStep)
 
 // ------------------------------------------------------------------ set-up
 // FCC lattice (N = 4 k^3, cell a = L/k, four-atom basis, offset a/4) and
@@ -145,11 +149,13 @@ __device__ void block_exclusive_scan(const int* cnt, int* start, int n, int* scr
 }
 
 // Cell binning and counting sort of all N atoms of a replica (whole block):
-// cstart[c]..cstart[c+1] index catoms, the atoms of cell c in increasing
-// index order (cells x-major, as ((cx * nc) + cy) * nc + cz).
+// cstart[c]..cstart[c+1] index spos, the atoms of cell c in increasing index
+// order (cells x-major, as ((cx * nc) + cy) * nc + cz); spos[k] holds the top
+// 32 bits of the position and, in .w, the atom index, so that the list build
+// scans contiguous ranges with one load per candidate.
 template <class PosFn>
-__device__ void cta_build_cells(PosFn pos_hi, int N, int nc, int* cstart, int* ccnt,
-                                uint16_t* catoms, uint16_t* acell, int* scratch) {
+__device__ void cta_build_cells(PosFn pos_hi, int N, int nc, int* cstart, int* ccnt, uint4* spos,
+                                uint16_t* acell, int* scratch) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int ncell = nc * nc * nc;
   for (int c = tid; c < ncell; c += T) ccnt[c] = 0;
@@ -165,19 +171,20 @@ __device__ void cta_build_cells(PosFn pos_hi, int N, int nc, int* cstart, int* c
   __syncthreads();
   for (int i = tid; i < N; i += T) {
     const int k = atomicAdd(&ccnt[acell[i]], 1);
-    catoms[k] = (uint16_t)i;
+    const Hi3 p = pos_hi(i);
+    spos[k] = make_uint4(p.x, p.y, p.z, (uint32_t)i);
   }
   __syncthreads();
   for (int c = tid; c < ncell; c += T) {
     const int b = cstart[c], e = cstart[c + 1];
     for (int k = b + 1; k < e; ++k) {
-      const uint16_t v = catoms[k];
+      const uint4 v = spos[k];
       int j = k - 1;
-      while (j >= b && catoms[j] > v) {
-        catoms[j + 1] = catoms[j];
+      while (j >= b && spos[j].w > v.w) {
+        spos[j + 1] = spos[j];
         --j;
       }
-      catoms[j + 1] = v;
+      spos[j + 1] = v;
     }
   }
   __syncthreads();
@@ -187,54 +194,6 @@ __device__ __forceinline__ float sep2_hi(Hi3 a, Hi3 b) {
   const float dx = (float)(int)(b.x - a.x), dy = (float)(int)(b.y - a.y),
               dz = (float)(int)(b.z - a.z);
   return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-}
-
-// Verlet list of atom i: every j != i closer than the list radius (squared,
-// in units of (L / 2^32)^2), scanned over the (2m+1)^3 neighbour cells (or
-// all atoms when nc == 0).  Entry k goes to nb[((k/4) * N + i) * 4 + k%4].
-// Returns the count; sets *overflow when more than cap were found.
-template <class PosFn>
-__device__ int build_atom_list(int i, PosFn pos_hi, int N, int nc, int m, const int* cstart,
-                               const uint16_t* catoms, float rl2u, uint16_t* nb, int cap,
-                               int* overflow) {
-  const Hi3 pi = pos_hi(i);
-  int cnt = 0;
-  if (nc == 0) {
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      if (sep2_hi(pi, pos_hi(j)) < rl2u) {
-        if (cnt < cap) nb[((size_t)(cnt >> 2) * N + i) * 4 + (cnt & 3)] = (uint16_t)j;
-        ++cnt;
-      }
-    }
-  } else {
-    const int cx = (int)__umulhi(pi.x, (uint32_t)nc), cy = (int)__umulhi(pi.y, (uint32_t)nc),
-              cz = (int)__umulhi(pi.z, (uint32_t)nc);
-    for (int ox = -m; ox <= m; ++ox) {
-      const int x = (cx + ox + nc) % nc;
-      for (int oy = -m; oy <= m; ++oy) {
-        const int y = (cy + oy + nc) % nc;
-        for (int oz = -m; oz <= m; ++oz) {
-          const int z = (cz + oz + nc) % nc;
-          const int c = (x * nc + y) * nc + z;
-          const int e = cstart[c + 1];
-          for (int k = cstart[c]; k < e; ++k) {
-            const int j = catoms[k];
-            if (j == i) continue;
-            if (sep2_hi(pi, pos_hi(j)) < rl2u) {
-              if (cnt < cap) nb[((size_t)(cnt >> 2) * N + i) * 4 + (cnt & 3)] = (uint16_t)j;
-              ++cnt;
-            }
-          }
-        }
-      }
-    }
-  }
-  if (cnt > cap) {
-    *overflow = 1;
-    cnt = cap;
-  }
-  return cnt;
 }
 
 // ------------------------------------------------------------------ forces
@@ -250,11 +209,11 @@ struct MixedAcc {
 
 __device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, float rc2u, float inv_lam2,
                                            MixedAcc& a) {
-  const float dx = i32_to_f32_split((int)(pj.x - pi.x));
-  const float dy = i32_to_f32_split((int)(pj.y - pi.y));
+  const float dx = (float)(int)(pj.x - pi.x);
+  const float dy = (float)(int)(pj.y - pi.y);
   const float dz = (float)(int)(pj.z - pi.z);
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  if (r2 < rc2u) {
+  if (r2 < rc2u && r2 > 0.0f) {  // r2 == 0: the atom itself (sub-list padding)
     const float s = rcp_approx(r2) * inv_lam2;
     const float s3 = s * s * s;
     const float fs = (s * s3) * fmaf(-48.0f, s3, 24.0f);
@@ -266,61 +225,18 @@ __device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, float rc2u, float
   }
 }
 
-__device__ __forceinline__ MixedAcc mixed_atom_forces(int i, const uint4* __restrict__ pos,
-                                                      const uint16_t* __restrict__ nb, int N,
-                                                      int cnt, float rc2u, float inv_lam2) {
-  MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
-  const uint4 pi = pos[i];
-  const int nblk = (cnt + 3) >> 2;
-  for (int kb = 0; kb < nblk; ++kb) {
-    const uint2 w = *reinterpret_cast<const uint2*>(nb + ((size_t)kb * N + i) * 4);
-    const int rem = cnt - 4 * kb;
-    const uint4 p0 = pos[w.x & 0xFFFFu];
-    const uint4 p1 = pos[rem > 1 ? (w.x >> 16) : i];
-    const uint4 p2 = pos[rem > 2 ? (w.y & 0xFFFFu) : i];
-    const uint4 p3 = pos[rem > 3 ? (w.y >> 16) : i];
-    mixed_pair(pi, p0, rc2u, inv_lam2, a);
-    if (rem > 1) mixed_pair(pi, p1, rc2u, inv_lam2, a);
-    if (rem > 2) mixed_pair(pi, p2, rc2u, inv_lam2, a);
-    if (rem > 3) mixed_pair(pi, p3, rc2u, inv_lam2, a);
-  }
-  return a;
-}
-
-// FP64 pair loop of atom i: separations are exact 64-bit minimum images
-// converted to double (units L / 2^64), pair force and energy in FP64.
+// Positions of the FP64 path: 64-bit fixed-point words (units L / 2^64).
 struct Pos64 {
   uint64_t x, y, z, w;
 };
-
-__device__ __forceinline__ void fp64_atom_forces(int i, Pos64 pi, const Pos64* pos,
-                                                 const uint16_t* nb, int N, int cnt, double lam64,
-                                                 double rc2, double uc, double& fx, double& fy,
-                                                 double& fz, double& e) {
-  fx = fy = fz = e = 0.0;
-  for (int k = 0; k < cnt; ++k) {
-    const int j = nb[((size_t)(k >> 2) * N + i) * 4 + (k & 3)];
-    const Pos64 pj = pos[j];
-    const double dx = (double)(long long)(pj.x - pi.x) * lam64;
-    const double dy = (double)(long long)(pj.y - pi.y) * lam64;
-    const double dz = (double)(long long)(pj.z - pi.z) * lam64;
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 < rc2) {
-      const double s = 1.0 / r2;
-      const double s3 = s * s * s;
-      const double fs = 48.0 * s3 * s3 * s - 24.0 * s3 * s;
-      fx -= fs * dx;
-      fy -= fs * dy;
-      fz -= fs * dz;
-      e += 4.0 * (s3 * s3 - s3) - uc;
-    }
-  }
-}
 
 // ------------------------------------------------------------------ batched
 struct StepConst {
   double lam32, lam64, inv_l, dtq, hdt, uc, rc2, c_th, kbar;
   float rc2u, rl2u, half2u, inv_lam2;
+  // thermostat constants of the mixed path (formed in FP64, used in FP32):
+  // c - 1, (1 - c) Kbar / Nf, 2 sqrt(c (1 - c) Kbar / Nf), sqrt(c Nf / ((1 - c) Kbar))
+  float cm1f, af, bf, gf;
   int nf;
 };
 
@@ -344,22 +260,30 @@ __device__ __forceinline__ StepConst step_const(const EnsDev& E, double T) {
   k.nf = 3 * E.N - 3;
   k.c_th = E.tau > 0.0 ? exp(-E.dt / E.tau) : 1.0;
   k.kbar = 0.5 * k.nf * T;
+  const double omc = E.tau > 0.0 ? -expm1(-E.dt / E.tau) : 0.0;  // 1 - c without cancellation
+  k.cm1f = (float)(-omc);
+  k.af = (float)(omc * k.kbar / k.nf);
+  k.bf = (float)(2.0 * sqrt(k.c_th * omc * k.kbar / k.nf));
+  k.gf = omc > 0.0 ? (float)sqrt(k.c_th * k.nf / (omc * k.kbar)) : 0.0f;
   return k;
 }
 
 struct BatchedSmem {
-  void* pos;      // uint4[N] (mixed) or Pos64[N] (fp64)
-  int* cstart;    // ncell + 1
-  int* ccnt;      // ncell
-  uint16_t* catoms;
+  void* pos;       // uint4[N] (mixed: top 32 bits of x, y, z) or Pos64[N] (fp64)
+  int* cstart;     // ncell + 1
+  int* ccnt;       // ncell
+  uint4* spos;     // cell-sorted positions (.w = atom index)
+  int* wscan;      // 2 x (threads + 1): block scan of own atoms in cell order
+  uint16_t* own_sorted;  // threads: sorted slots of this CTA's atoms
+  int* cnt_sh;     // threads: sub-list counts handed to the owners
+  long long* rec_k;  // kNoiseChunk: 2K of each step (fixed point), CTA 0
+  float* rec_e;      // kNoiseChunk: alpha - 1 of each step
   uint16_t* acell;
-  double2* noise; // threads
-  float* slot_md; // [cluster][warps]
-  double* slot_uk;// [cluster][warps][2]
-  int* slot_st;   // [cluster]
-  double* red;    // 64
-  int* iscr;      // 64
-  double* bcast;  // 8
+  double2* noise;  // 2 x kNoiseChunk thermostat records (double buffered)
+  float* slot_md;  // [cluster][warps]
+  double* slot_uk; // [cluster][warps][2]
+  int* slot_st;    // [cluster]
+  int* iscr;       // 64
 };
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -374,29 +298,39 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
     return o;
   };
   const size_t o_pos = take((size_t)max_n * (fp64 ? 32 : 16), 32);
-  const size_t o_noise = take((size_t)threads * 16, 16);
+  const size_t o_sp = take((size_t)max_n * 16, 16);
+  const size_t o_noise = take((size_t)kNoiseChunk * 2 * kSvrStepBytes, 16);
   const size_t o_uk = take((size_t)kMaxCluster * kMaxWarps * 2 * 8, 16);
-  const size_t o_red = take(64 * 8, 8);
-  const size_t o_bc = take(8 * 8, 8);
   const size_t o_md = take((size_t)kMaxCluster * kMaxWarps * 4, 4);
   const size_t o_st = take(kMaxCluster * 4, 4);
   const size_t o_isc = take(64 * 4, 4);
+  const size_t o_rk = take((size_t)kNoiseChunk * 8, 8);
+  const size_t o_re = take((size_t)kNoiseChunk * 4, 4);
   const size_t o_cs = take((size_t)(max_ncell + 1) * 4, 4);
   const size_t o_cc = take((size_t)(max_ncell + 1) * 4, 4);
-  const size_t o_ca = take((size_t)max_n * 2, 2);
-  const size_t o_ac = take((size_t)max_n * 2, 2);
+  // one region, two lifetimes: the atoms' cell ids during the cell sort, then
+  // the block scan, the own-slot list and the hand-over counts of the list build
+  const size_t scan_bytes = (size_t)2 * (threads + 1) * 4 + (size_t)threads * 4 + (size_t)threads * 2;
+  const size_t o_un = take(scan_bytes > (size_t)max_n * 2 ? scan_bytes : (size_t)max_n * 2, 4);
+  const size_t o_ws = o_un;
+  const size_t o_cn = o_un + (size_t)2 * (threads + 1) * 4;
+  const size_t o_os = o_cn + (size_t)threads * 4;
+  const size_t o_ac = o_un;
   if (out) {
     out->pos = base + o_pos;
     out->noise = reinterpret_cast<double2*>(base + o_noise);
     out->slot_uk = reinterpret_cast<double*>(base + o_uk);
-    out->red = reinterpret_cast<double*>(base + o_red);
-    out->bcast = reinterpret_cast<double*>(base + o_bc);
     out->slot_md = reinterpret_cast<float*>(base + o_md);
     out->slot_st = reinterpret_cast<int*>(base + o_st);
     out->iscr = reinterpret_cast<int*>(base + o_isc);
+    out->rec_k = reinterpret_cast<long long*>(base + o_rk);
+    out->rec_e = reinterpret_cast<float*>(base + o_re);
     out->cstart = reinterpret_cast<int*>(base + o_cs);
     out->ccnt = reinterpret_cast<int*>(base + o_cc);
-    out->catoms = reinterpret_cast<uint16_t*>(base + o_ca);
+    out->spos = reinterpret_cast<uint4*>(base + o_sp);
+    out->wscan = reinterpret_cast<int*>(base + o_ws);
+    out->cnt_sh = reinterpret_cast<int*>(base + o_cn);
+    out->own_sorted = reinterpret_cast<uint16_t*>(base + o_os);
     out->acell = reinterpret_cast<uint16_t*>(base + o_ac);
   }
   return align_up(off, 128);
@@ -406,33 +340,259 @@ struct KernelDims {
   int max_n, max_ncell;
 };
 
-// One thread-block cluster per replica (work item).  CTA `crank` of the
-// cluster owns atoms [i0, i1) and keeps the positions of all N atoms of the
-// replica in its shared memory; each step it broadcasts its own atoms' new
-// positions to every CTA of the cluster.  Two cluster barriers per step: after
-// the drift (positions and displacement maxima visible) and after the second
-// kick (energy partial sums visible; all position reads of the step done).
-template <bool FP64>
-__global__ void __launch_bounds__(512, 1) md_batched_kernel(StateDev S,
-                                                          const EnsDev* __restrict__ ens,
-                                                          const RepDev* __restrict__ reps,
-                                                          const int* __restrict__ work,
-                                                          const int32_t* __restrict__ budget,
-                                                          KernelDims dims) {
+__device__ __forceinline__ uint64_t* qcomp(const StateDev& S, int d) {
+  return d == 0 ? S.qx : (d == 1 ? S.qy : S.qz);
+}
+__device__ __forceinline__ double* vcomp(const StateDev& S, int d) {
+  return d == 0 ? S.vx : (d == 1 ? S.vy : S.vz);
+}
+__device__ __forceinline__ double* fcomp(const StateDev& S, int d) {
+  return d == 0 ? S.fx : (d == 1 ? S.fy : S.fz);
+}
+__device__ __forceinline__ uint32_t* rcomp(const StateDev& S, int d) {
+  return d == 0 ? S.rx : (d == 1 ? S.ry : S.rz);
+}
+
+// Sub-list of lane q (of P) of atom i: candidates of every scanned range are
+// dealt to the P lanes in turn (candidate k of a range goes to lane k % P).
+// Entry k of sub-list (i, q) sits at nb[((k/4) * N*P + i*P + q) * 4 + k%4].
+template <int P, class PosFn>
+__device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, const int* cstart,
+                             const uint4* spos, float rl2u, uint16_t* nb, int cap_sub,
+                             int* overflow) {
+  const Hi3 pi = pos_hi(i);
+  const size_t stride = (size_t)N * P;
+  const size_t col = (size_t)i * P + q;
+  int cnt = 0;
+  auto accept = [&](int j, Hi3 pj) {
+    const float r2 = sep2_hi(pi, pj);
+    if (j != i && r2 < rl2u) {
+      // two distinct atoms at one point (closer than L / 2^32): the pair loop
+      // treats distance 0 as the sub-list padding, so report it here
+      if (r2 == 0.0f) *overflow |= kStNumeric;
+      if (cnt < cap_sub) nb[((size_t)(cnt >> 2) * stride + col) * 4 + (cnt & 3)] = (uint16_t)j;
+      ++cnt;
+    }
+  };
+  if (nc == 0) {
+    for (int j = q; j < N; j += P) accept(j, pos_hi(j));
+  } else {
+    const int cx = (int)__umulhi(pi.x, (uint32_t)nc), cy = (int)__umulhi(pi.y, (uint32_t)nc),
+              cz = (int)__umulhi(pi.z, (uint32_t)nc);
+    // cells z in [cz - m, cz + m] (periodic) are at most two contiguous ranges
+    // of the cell order: [lo1, hi1) and [0, hi2) (empty when hi2 == 0)
+    const int zlo = cz - m, zhi = cz + m;
+    const int lo1 = zlo < 0 ? zlo + nc : zlo;
+    const int hi1 = (zlo < 0 || zhi >= nc) ? nc : zhi + 1;
+    const int hi2 = zlo < 0 ? zhi + 1 : (zhi >= nc ? zhi - nc + 1 : 0);
+    for (int ox = -m; ox <= m; ++ox) {
+      int x = cx + ox;
+      x += (x < 0) ? nc : 0;
+      x -= (x >= nc) ? nc : 0;
+      for (int oy = -m; oy <= m; ++oy) {
+        int y = cy + oy;
+        y += (y < 0) ? nc : 0;
+        y -= (y >= nc) ? nc : 0;
+        const int base = (x * nc + y) * nc;
+        const int b1 = cstart[base + lo1], e1 = cstart[base + hi1];
+        const int b2 = cstart[base], e2 = cstart[base + hi2];
+        const int n1 = e1 - b1, n = n1 + (e2 - b2);
+        for (int t = q; t < n; t += P) {
+          const uint4 v = spos[t < n1 ? b1 + t : b2 + (t - n1)];
+          accept((int)v.w, Hi3{v.x, v.y, v.z});
+        }
+      }
+    }
+  }
+  if (cnt > cap_sub) {
+    *overflow |= kStOverflow;
+    cnt = cap_sub;
+  }
+  // pad to a whole block of four with the atom's own index (skipped by r2 > 0)
+  for (int k = cnt; k & 3; ++k) nb[((size_t)(k >> 2) * stride + col) * 4 + (k & 3)] = (uint16_t)i;
+  return cnt;
+}
+
+// Mixed-precision sub-list loop of lane (i, q); see mixed_pair.
+// Sub-lists are padded with the atom's own index up to a whole block of four,
+// so every block is processed without per-entry tests.
+template <int P>
+__device__ __forceinline__ MixedAcc mixed_sublist_forces(int i, int q, uint4 pi,
+                                                         const uint4* __restrict__ pos,
+                                                         const uint16_t* __restrict__ nb, int N,
+                                                         int cnt, float rc2u, float inv_lam2) {
+  MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
+  const size_t stride4 = (size_t)N * P * 4;
+  const uint16_t* base = nb + ((size_t)i * P + q) * 4;
+  const int nblk = (cnt + 3) >> 2;
+  uint2 w = nblk > 0 ? *reinterpret_cast<const uint2*>(base) : make_uint2(0u, 0u);
+  for (int kb = 0; kb < nblk; ++kb) {
+    // the next block of indices is requested before this block is used
+    const uint2 wn = kb + 1 < nblk ? *reinterpret_cast<const uint2*>(base + (size_t)(kb + 1) * stride4) : w;
+    const uint4 p0 = pos[w.x & 0xFFFFu];
+    const uint4 p1 = pos[w.x >> 16];
+    const uint4 p2 = pos[w.y & 0xFFFFu];
+    const uint4 p3 = pos[w.y >> 16];
+    mixed_pair(pi, p0, rc2u, inv_lam2, a);
+    mixed_pair(pi, p1, rc2u, inv_lam2, a);
+    mixed_pair(pi, p2, rc2u, inv_lam2, a);
+    mixed_pair(pi, p3, rc2u, inv_lam2, a);
+    w = wn;
+  }
+  return a;
+}
+
+template <int P>
+__device__ __forceinline__ void fp64_sublist_forces(int i, int q, Pos64 pi, const Pos64* pos,
+                                                    const uint16_t* nb, int N, int cnt,
+                                                    double lam64, double rc2, double uc,
+                                                    double& fx, double& fy, double& fz,
+                                                    double& e) {
+  fx = fy = fz = e = 0.0;
+  const size_t stride = (size_t)N * P;
+  const size_t col = (size_t)i * P + q;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = nb[((size_t)(k >> 2) * stride + col) * 4 + (k & 3)];
+    const Pos64 pj = pos[j];
+    const double dx = (double)(long long)(pj.x - pi.x) * lam64;
+    const double dy = (double)(long long)(pj.y - pi.y) * lam64;
+    const double dz = (double)(long long)(pj.z - pi.z) * lam64;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < rc2) {
+      const double s = 1.0 / r2;
+      const double s3 = s * s * s;
+      const double fs = 48.0 * s3 * s3 * s - 24.0 * s3 * s;
+      fx -= fs * dx;
+      fy -= fs * dy;
+      fz -= fs * dz;
+      e += 4.0 * (s3 * s3 - s3) - uc;
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = 1; o < P; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int P>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = 1; o < P; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int P>
+__device__ __forceinline__ int group_sum(int v) {
+#pragma unroll
+  for (int o = 1; o < P; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-step thermostat constants, computed ahead of the step (off the critical
+// path).  With K the kinetic energy after the second half kick, the SVR update
+// is K'/K = 1 + delta with delta = (c - 1) + (a + b sqrt(K)) / K, where
+// a = (1 - c) Kbar (R1^2 + S) / Nf and b = 2 R1 sqrt(c (1 - c) Kbar / Nf); the
+// factor alpha = +-sqrt(1 + delta) is negative when R1 + g sqrt(K) < 0,
+// g = sqrt(c Nf / ((1 - c) Kbar)).
+struct SvrStep {
+  double r1, s;        // the draws (FP64 path)
+  float cm1, a, b, g;  // the constants above (mixed path)
+  float r1f;           // R1 (mixed path)
+  int bad;             // the Gamma sampler hit its trial cap
+};
+static_assert(sizeof(SvrStep) == kSvrStepBytes, "thermostat record size");
+
+__device__ inline SvrStep svr_step(bool fp64, const StepConst& K, uint64_t seed, uint64_t stream,
+                                   uint64_t n, int* capped) {
+  SvrStep t;
+  t.cm1 = K.cm1f;
+  t.g = K.gf;
+  t.bad = 0;
+  if (fp64) {
+    const double2 z = svr_noise(K.nf, seed, stream, n, capped);
+    t.r1 = z.x;
+    t.s = z.y;
+    t.a = t.b = 0.0f;
+    t.r1f = (float)z.x;
+  } else {
+    const float2 z = svr_noise_f32(K.nf, seed, stream, n, capped);
+    t.r1 = z.x;
+    t.s = z.y;
+    t.a = K.af * fmaf(z.x, z.x, z.y);
+    t.b = K.bf * z.x;
+    t.r1f = z.x;
+  }
+  return t;
+}
+
+// alpha - 1 in FP32 without cancellation: sqrt(1 + delta) - 1 = delta / (1 + sqrt(1 + delta)).
+__device__ __forceinline__ float svr_eps(const SvrStep& t, float Kf) {
+  const float sk = sqrtf(Kf);
+  const float delta = t.cm1 + (t.a + t.b * sk) / Kf;
+  const float root = sqrtf(1.0f + delta);
+  if (t.r1f + t.g * sk < 0.0f) return -1.0f - root;  // alpha = -sqrt(1 + delta)
+  return delta / (1.0f + root);
+}
+
+// Fixed-point scales of the mixed path: velocities in units of 2^-48 (64-bit,
+// |v| < 2^15), energy partial sums in units of 2^-28 (64-bit, |sum| < 2^35).
+constexpr float kVelScale = 281474976710656.0f;        // 2^48
+constexpr float kVelUnit = 3.5527136788005009e-15f;   // 2^-48
+constexpr float kEnScale = 268435456.0f;              // 2^28
+constexpr double kEnUnit = 3.7252902984619140625e-09; // 2^-28
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One thread-block cluster per replica (work item).  CTA `crank` owns atoms
+// [i0, i1); P consecutive lanes serve one atom: lane q keeps the state of the
+// coordinates d = q, q + P, ... in registers for the whole launch and owns one
+// sub-list of the atom's Verlet list.  Every CTA keeps the positions of all N
+// atoms of the replica in shared memory (top 32 bits, or all 64 bits on the
+// FP64 path); each step the owners broadcast their new coordinates to every
+// CTA of the cluster.  Two cluster barriers per step: after the drift
+// (positions and displacement maxima visible) and after the second kick
+// (energy partial sums visible; all position reads of the step done).
+//
+// Mixed path: positions and velocities are 64-bit fixed-point master copies
+// updated with FP32 increments (exact accumulation; FP64 arithmetic runs at
+// 1/64 of the FP32 rate on this GPU); pair forces FP32; energy sums 64-bit
+// integers (exact, order independent).  The second half kick, the thermostat
+// factor and the next first half kick form one increment per coordinate.
+// FP64 path: FP64 state arithmetic and FP64 pair forces throughout.
+template <bool FP64, int P>
+__global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
+                                                             const EnsDev* __restrict__ ens,
+                                                             const RepDev* __restrict__ reps,
+                                                             const int* __restrict__ work,
+                                                             const int32_t* __restrict__ budget,
+                                                             KernelDims dims) {
+  constexpr int ND = (3 + P - 1) / P;  // coordinates per lane
+  // replica constants live in shared memory, not in registers
+  __shared__ EnsDev E;
+  __shared__ StepConst K;
+  __shared__ double alpha_sh, kp_sh;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const int r = work[blockIdx.x / C];
   const RepDev rd = reps[r];
-  const EnsDev E = ens[rd.ens];
-  const int N = E.N, T = blockDim.x, tid = threadIdx.x;
+  if (threadIdx.x == 0) {
+    E = ens[rd.ens];
+    K = step_const(E, S.T[r]);
+  }
+  const int T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nw = (T + 31) >> 5;
+  const int q = tid & (P - 1);
   const int B = budget[r];
   const int status0 = S.status[r];
   const int valid0 = S.valid[r];
-  double vs = S.vscale[r];
+  const double vs0 = S.vscale[r];
   double econs = S.econs[r];
-  const double Ttarget = S.T[r];
   const int64_t step0 = S.step[r];
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -441,104 +601,232 @@ __global__ void __launch_bounds__(512, 1) md_batched_kernel(StateDev S,
   uint4* posm = reinterpret_cast<uint4*>(sm.pos);
   Pos64* pos64 = reinterpret_cast<Pos64*>(sm.pos);
 
-  // Every CTA has read the replica's flags before any CTA may change them.
+  // Every CTA has read the replica's flags before any CTA may change them
+  // (the barrier also publishes E and K to the whole CTA).
   cl.sync();
   if (status0 != 0 || (B <= 0 && valid0)) return;  // uniform over the cluster
+  // a one-CTA replica synchronises with the cheaper block barrier
+  auto csync = [&]() {
+    if (C > 1)
+      cl.sync();
+    else
+      __syncthreads();
+  };
 
-  const StepConst K = step_const(E, Ttarget);
+  const int N = E.N;
   const int per = (N + C - 1) / C;
   const int i0 = min(N, crank * per), i1 = min(N, i0 + per);
-  const int aoff = rd.atom_off;
+  const int i = i0 + tid / P;
+  const bool own = i < i1;
+  const int g = rd.atom_off + i;
+  const int cap_sub = E.capsub[P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : 3))];
   uint16_t* nb = S.nbr + rd.nbr_off;
+  int32_t* ncnt = S.ncnt + (size_t)rd.atom_off * 8;
+  const float hl = (float)(K.hdt * K.lam32);  // FP32 half-kick factor per force unit
+  const float dtqf = (float)K.dtq;
+  const float ucf = (float)K.uc;
+  const bool thermo = E.tau > 0.0;  // decided once; no FP64 tests inside the step loop
 
-  auto hi_of = [&](int i) -> Hi3 {
+  // per-lane state in registers
+  uint64_t xq[ND];
+  double v[ND], f[ND];       // FP64 path
+  long long vq[ND];          // mixed path: velocity, fixed point
+  float vf[ND], hf[ND];      // mixed path: FP32 velocity copy, half-kick increment
+  uint32_t ref[ND];
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    const int d = q + j * P;
+    xq[j] = 0;
+    v[j] = f[j] = 0.0;
+    vq[j] = 0;
+    vf[j] = hf[j] = 0.0f;
+    ref[j] = 0;
+    if (own && d < 3) {
+      xq[j] = qcomp(S, d)[g];
+      const double vv = vcomp(S, d)[g] * vs0;
+      const double ff = fcomp(S, d)[g];
+      ref[j] = rcomp(S, d)[g];
+      if (FP64) {
+        v[j] = vv;
+        f[j] = ff;
+      } else {
+        vq[j] = __double2ll_rn(vv * 0x1.0p48);  // once per launch
+        vf[j] = (float)vv;
+        hf[j] = (float)(ff * K.hdt);
+      }
+    }
+  }
+  if (own) cnt = ncnt[(size_t)i * P + q];
+
+  auto hi_of = [&](int a) -> Hi3 {
     if (FP64) {
-      const Pos64 p = pos64[i];
+      const Pos64 p = pos64[a];
       return Hi3{(uint32_t)(p.x >> 32), (uint32_t)(p.y >> 32), (uint32_t)(p.z >> 32)};
     } else {
-      const uint4 p = posm[i];
+      const uint4 p = posm[a];
       return Hi3{p.x, p.y, p.z};
     }
   };
-  auto publish = [&](int i, uint64_t qx, uint64_t qy, uint64_t qz) {
-    if (FP64) {
-      const Pos64 p{qx, qy, qz, 0ull};
-      for (int q = 0; q < C; ++q) cl.map_shared_rank(pos64, q)[i] = p;
-    } else {
-      const uint4 p = make_uint4((uint32_t)(qx >> 32), (uint32_t)(qy >> 32),
-                                 (uint32_t)(qz >> 32), 0u);
-      for (int q = 0; q < C; ++q) cl.map_shared_rank(posm, q)[i] = p;
+  // broadcast this lane's coordinates of atom i to every CTA of the cluster
+  auto publish = [&]() {
+    if (!own) return;
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int d = q + j * P;
+      if (d >= 3) continue;
+      if (FP64) {
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&pos64[i]) + d;
+        for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(dst, rk) = xq[j];
+      } else {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&posm[i]) + d;
+        const uint32_t hv = (uint32_t)(xq[j] >> 32);
+        for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(dst, rk) = hv;
+      }
     }
   };
 
-  // Rebuild of the lists of this CTA's atoms (cells built redundantly per CTA).
   int overflow = 0;
   int nreb = 0;
+  // Rebuild of the lists of this CTA's atoms.  With cells, the lane groups take
+  // this CTA's atoms in cell order (neighbouring lanes then scan the same cell
+  // ranges) and hand the sub-list counts to the owners through shared memory.
   auto rebuild = [&]() {
-    if (E.nc > 0)
-      cta_build_cells(hi_of, N, E.nc, sm.cstart, sm.ccnt, sm.catoms, sm.acell, sm.iscr);
-    for (int i = i0 + tid; i < i1; i += T) {
-      const int g = aoff + i;
-      const int cnt = build_atom_list(i, hi_of, N, E.nc, E.m, sm.cstart, sm.catoms, K.rl2u, nb,
-                                      E.cap, &overflow);
-      S.ncnt[g] = cnt;
-      const Hi3 p = hi_of(i);
-      S.rx[g] = p.x;
-      S.ry[g] = p.y;
-      S.rz[g] = p.z;
+    if (E.nc > 0) {
+      cta_build_cells(hi_of, N, E.nc, sm.cstart, sm.ccnt, sm.spos, sm.acell, sm.iscr);
+      int n_own = i1 - i0;
+      if (C > 1) {
+        const int pt = (N + T - 1) / T;
+        const int lo = min(N, tid * pt), hi = min(N, lo + pt);
+        int c = 0;
+        for (int k = lo; k < hi; ++k) {
+          const int a = (int)sm.spos[k].w;
+          c += (a >= i0 && a < i1);
+        }
+        sm.wscan[tid] = c;
+        __syncthreads();
+        block_exclusive_scan(sm.wscan, sm.wscan + T + 1, T, sm.iscr);
+        int at = sm.wscan[T + 1 + tid];
+        for (int k = lo; k < hi; ++k) {
+          const int a = (int)sm.spos[k].w;
+          if (a >= i0 && a < i1) sm.own_sorted[at++] = (uint16_t)k;
+        }
+        __syncthreads();
+      }
+      const int gi = tid / P;
+      if (gi < n_own) {
+        // one CTA: every sorted slot is its own; several: the compacted slots
+        const int a = (int)sm.spos[C == 1 ? gi : (int)sm.own_sorted[gi]].w;
+        const int c = build_sublist<P>(a, q, hi_of, N, E.nc, E.m, sm.cstart, sm.spos, K.rl2u, nb,
+                                       cap_sub, &overflow);
+        sm.cnt_sh[(a - i0) * P + q] = c;
+      }
+      __syncthreads();
+      if (own) cnt = sm.cnt_sh[(i - i0) * P + q];
+    } else if (own) {
+      cnt = build_sublist<P>(i, q, hi_of, N, E.nc, E.m, sm.cstart, sm.spos, K.rl2u, nb, cap_sub,
+                             &overflow);
+    }
+    if (own) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) ref[j] = (uint32_t)(xq[j] >> 32);
     }
     ++nreb;
   };
 
-  // Forces of this CTA's atoms (and optionally the second half kick); returns
-  // this thread's partial U (per-atom energies, full list) and K (sum v^2).
-  auto forces = [&](bool kick, double& u_part, double& k_part) {
-    u_part = 0.0;
-    k_part = 0.0;
-    for (int i = i0 + tid; i < i1; i += T) {
-      const int g = aoff + i;
-      const int cnt = S.ncnt[g];
-      double fx, fy, fz, e;
-      if (FP64) {
-        fp64_atom_forces(i, pos64[i], pos64, nb, N, cnt, K.lam64, K.rc2, K.uc, fx, fy, fz, e);
-      } else {
-        const MixedAcc a = mixed_atom_forces(i, posm, nb, N, cnt, K.rc2u, K.inv_lam2);
-        fx = (double)a.fx * K.lam32;
-        fy = (double)a.fy * K.lam32;
-        fz = (double)a.fz * K.lam32;
-        e = (double)a.e - K.uc * (double)a.nin;
+  // Forces on this lane's atom (sub-list sums combined over the P lanes) and
+  // the second half kick when `kick`.  Publishes this warp's partial sums of
+  // U and of v^2 (after the kick) to every CTA; returns the lanes' numeric flag.
+  auto forces_and_publish = [&](bool kick, int st_in) {
+    int st = st_in;
+    long long iu = 0, ik = 0;  // mixed: fixed-point partial sums
+    double du = 0.0, dk = 0.0; // FP64 path
+    if (FP64) {
+      double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
+      if (own)
+        fp64_sublist_forces<P>(i, q, pos64[i], pos64, nb, N, cnt, K.lam64, K.rc2, K.uc, fx, fy, fz,
+                               e);
+      fx = group_sum<P>(fx);
+      fy = group_sum<P>(fy);
+      fz = group_sum<P>(fz);
+      e = group_sum<P>(e);
+      if (own) {
+        if (q == 0) du = e;
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const int d = q + j * P;
+          if (d >= 3) continue;
+          f[j] = d == 0 ? fx : (d == 1 ? fy : fz);
+          if (kick) v[j] += K.hdt * f[j];
+          dk += v[j] * v[j];
+        }
       }
-      S.fx[g] = fx;
-      S.fy[g] = fy;
-      S.fz[g] = fz;
-      u_part += e;
-      double vx = S.vx[g], vy = S.vy[g], vz = S.vz[g];
-      if (kick) {
-        vx += K.hdt * fx;
-        vy += K.hdt * fy;
-        vz += K.hdt * fz;
-        S.vx[g] = vx;
-        S.vy[g] = vy;
-        S.vz[g] = vz;
+      du = warp_sum(du);
+      dk = warp_sum(dk);
+    } else {
+      MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
+      if (own) a = mixed_sublist_forces<P>(i, q, posm[i], posm, nb, N, cnt, K.rc2u, K.inv_lam2);
+      const float ax = group_sum<P>(a.fx), ay = group_sum<P>(a.fy), az = group_sum<P>(a.fz);
+      const float ae = group_sum<P>(a.e) - ucf * (float)group_sum<P>(a.nin);
+      if (own) {
+        if (q == 0) {
+          if (!isfinite(ae)) st |= kStNumeric;
+          iu = f2ll_split(ae * kEnScale);
+        }
+        float kl = 0.0f;
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const int d = q + j * P;
+          if (d >= 3) continue;
+          hf[j] = (d == 0 ? ax : (d == 1 ? ay : az)) * hl;
+          const float w = kick ? vf[j] + hf[j] : vf[j];
+          kl = fmaf(w, w, kl);
+        }
+        if (!isfinite(kl)) st |= kStNumeric;
+        ik = f2ll_split(kl * kEnScale);
       }
-      k_part += vx * vx + vy * vy + vz * vz;
+      iu = warp_sum_i64(iu);
+      ik = warp_sum_i64(ik);
     }
-  };
-
-  // Publish per-warp partial sums to every CTA, then (after the barrier) warp 0
-  // of each CTA sums them in a fixed order.
-  auto publish_uk = [&](double u, double kk, int st) {
-    u = warp_sum(u);
-    kk = warp_sum(kk);
     st = warp_or(st);
     if (lane == 0) {
-      for (int q = 0; q < C; ++q) {
-        double* uk = cl.map_shared_rank(sm.slot_uk, q);
-        uk[(crank * kMaxWarps + warp) * 2 + 0] = u;
-        uk[(crank * kMaxWarps + warp) * 2 + 1] = kk;
-        if (st) atomicOr(cl.map_shared_rank(sm.slot_st, q) + crank, st);
+      for (int rk = 0; rk < C; ++rk) {
+        long long* uk = reinterpret_cast<long long*>(cl.map_shared_rank(sm.slot_uk, rk));
+        uk[(crank * kMaxWarps + warp) * 2 + 0] = FP64 ? __double_as_longlong(du) : iu;
+        uk[(crank * kMaxWarps + warp) * 2 + 1] = FP64 ? __double_as_longlong(dk) : ik;
+        if (st) atomicOr(cl.map_shared_rank(sm.slot_st, rk) + crank, st);
       }
     }
+  };
+  // Every warp sums the published partials in the same fixed order and reads
+  // the status bits of every CTA.  FP64 path: sums of FP64 values.  Mixed
+  // path: exact 64-bit integer sums of the fixed-point partials.
+  auto totals_fp64 = [&](double& su, double& sk, int& st) {
+    const long long* uk = reinterpret_cast<const long long*>(sm.slot_uk);
+    su = 0.0;
+    sk = 0.0;
+    for (int idx = lane; idx < C * kMaxWarps; idx += 32)
+      if (idx % kMaxWarps < nw) {
+        su += __longlong_as_double(uk[idx * 2 + 0]);
+        sk += __longlong_as_double(uk[idx * 2 + 1]);
+      }
+    su = warp_sum(su);
+    sk = warp_sum(sk);
+    st = 0;
+    for (int rk = 0; rk < C; ++rk) st |= sm.slot_st[rk];
+  };
+  auto totals_int = [&](long long& iu, long long& ik, int& st) {
+    const long long* uk = reinterpret_cast<const long long*>(sm.slot_uk);
+    long long a = 0, b = 0;
+    for (int idx = lane; idx < C * kMaxWarps; idx += 32)
+      if (idx % kMaxWarps < nw) {
+        a += uk[idx * 2 + 0];
+        b += uk[idx * 2 + 1];
+      }
+    iu = warp_sum_i64(a);
+    ik = warp_sum_i64(b);
+    st = 0;
+    for (int rk = 0; rk < C; ++rk) st |= sm.slot_st[rk];
   };
 
   if (tid < C) sm.slot_st[tid] = 0;
@@ -547,137 +835,167 @@ __global__ void __launch_bounds__(512, 1) md_batched_kernel(StateDev S,
   int status = 0;
 
   if (!valid0) {
-    // Prologue: apply any pending velocity factor, build lists, forces, U, K.
-    for (int i = i0 + tid; i < i1; i += T) {
-      const int g = aoff + i;
-      if (vs != 1.0) {
-        S.vx[g] *= vs;
-        S.vy[g] *= vs;
-        S.vz[g] *= vs;
-      }
-      publish(i, S.qx[g], S.qy[g], S.qz[g]);
-    }
-    vs = 1.0;
-    cl.sync();
+    // Prologue: lists, forces, U and K at the current positions.
+    publish();
+    csync();
     rebuild();
-    double u, kk;
-    forces(false, u, kk);
-    publish_uk(u, kk, overflow ? kStOverflow : 0);
-    cl.sync();
-    if (warp == 0) {
-      double su = 0.0, sk = 0.0;
-      for (int idx = lane; idx < C * kMaxWarps; idx += 32) {
-        const int q = idx / kMaxWarps, w = idx % kMaxWarps;
-        if (w < nw) {
-          su += sm.slot_uk[(q * kMaxWarps + w) * 2 + 0];
-          sk += sm.slot_uk[(q * kMaxWarps + w) * 2 + 1];
-        }
-      }
-      su = warp_sum(su);
-      sk = warp_sum(sk);
-      if (lane == 0) {
-        sm.bcast[0] = 0.5 * su;
-        sm.bcast[1] = 0.5 * sk;
-        int st = 0;
-        for (int q = 0; q < C; ++q) st |= sm.slot_st[q];
-        sm.bcast[2] = (double)st;
-      }
+    forces_and_publish(false, overflow);
+    csync();
+    if (FP64) {
+      double su, sk;
+      totals_fp64(su, sk, status);
+      U = 0.5 * su;
+      Kin = 0.5 * sk;
+      if (!isfinite(U) || !isfinite(Kin)) status |= kStNumeric;
+    } else {
+      long long iu, ik;
+      totals_int(iu, ik, status);
+      U = 0.5 * (double)iu * kEnUnit;  // FP64 only for the stored energies
+      Kin = 0.5 * (double)ik * kEnUnit;
     }
-    __syncthreads();
-    U = sm.bcast[0];
-    Kin = sm.bcast[1];
-    status = (int)sm.bcast[2];
-    if (!isfinite(U) || !isfinite(Kin)) status |= kStNumeric;
   }
 
   int done = 0;
   for (int s = 0; s < B && status == 0; ++s) {
     const int64_t n = step0 + s;
-    if (E.tau > 0.0 && (s % T) == 0 && s + tid < B) {
+    SvrStep* sv = reinterpret_cast<SvrStep*>(sm.noise) + ((s / kNoiseChunk) & 1) * kNoiseChunk;
+    if (thermo && (s % kNoiseChunk) == 0 && tid < kNoiseChunk && s + tid < B) {
       int capped = 0;
-      sm.noise[tid] = svr_noise(K.nf, E.seed, (uint64_t)rd.id, (uint64_t)(n + tid), &capped);
-      if (capped) sm.noise[tid].y = -1.0;
+      SvrStep z = svr_step(FP64, K, E.seed, (uint64_t)rd.id, (uint64_t)(n + tid), &capped);
+      z.bad = capped;
+      sv[tid] = z;
     }
-    // kick + drift + displacement since the last rebuild
-    float md = 0.0f;
-    for (int i = i0 + tid; i < i1; i += T) {
-      const int g = aoff + i;
-      const double vx = fma(S.vx[g], vs, K.hdt * S.fx[g]);
-      const double vy = fma(S.vy[g], vs, K.hdt * S.fy[g]);
-      const double vz = fma(S.vz[g], vs, K.hdt * S.fz[g]);
-      S.vx[g] = vx;
-      S.vy[g] = vy;
-      S.vz[g] = vz;
-      const uint64_t qx = S.qx[g] + (uint64_t)__double2ll_rn(vx * K.dtq);
-      const uint64_t qy = S.qy[g] + (uint64_t)__double2ll_rn(vy * K.dtq);
-      const uint64_t qz = S.qz[g] + (uint64_t)__double2ll_rn(vz * K.dtq);
-      S.qx[g] = qx;
-      S.qy[g] = qy;
-      S.qz[g] = qz;
-      publish(i, qx, qy, qz);
-      const Hi3 ref{S.rx[g], S.ry[g], S.rz[g]};
-      const Hi3 now{(uint32_t)(qx >> 32), (uint32_t)(qy >> 32), (uint32_t)(qz >> 32)};
-      md = fmaxf(md, sep2_hi(ref, now));
+    // (first half kick of the launch) + drift + displacement since the last rebuild
+    float d2 = 0.0f;
+    if (own) {
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        const int d = q + j * P;
+        if (d >= 3) continue;
+        if (FP64) {
+          if (s == 0) v[j] += K.hdt * f[j];
+          xq[j] += (uint64_t)__double2ll_rn(v[j] * K.dtq);
+        } else {
+          if (s == 0) {
+            vq[j] += f2ll_split(hf[j] * kVelScale);
+            vf[j] = ll2f_split(vq[j]) * kVelUnit;
+          }
+          xq[j] += (uint64_t)f2ll_split(vf[j] * dtqf);
+        }
+        const float dd = (float)(int)((uint32_t)(xq[j] >> 32) - ref[j]);
+        d2 = fmaf(dd, dd, d2);
+      }
     }
-    vs = 1.0;
-    md = warp_max(md);
+    publish();
+    d2 = group_sum<P>(d2);
+    float md = warp_max(d2);
     if (lane == 0)
-      for (int q = 0; q < C; ++q) cl.map_shared_rank(sm.slot_md, q)[crank * kMaxWarps + warp] = md;
-    cl.sync();  // B1
+      for (int rk = 0; rk < C; ++rk)
+        cl.map_shared_rank(sm.slot_md, rk)[crank * kMaxWarps + warp] = md;
+    csync();  // B1
     float mdall = 0.0f;
     for (int idx = lane; idx < C * kMaxWarps; idx += 32)
       if (idx % kMaxWarps < nw) mdall = fmaxf(mdall, sm.slot_md[idx]);
     mdall = warp_max(mdall);
     if (mdall > K.half2u) rebuild();
-    double u, kk;
-    forces(true, u, kk);
-    publish_uk(u, kk, overflow ? kStOverflow : 0);
-    cl.sync();  // B2
-    if (warp == 0) {
-      double su = 0.0, sk = 0.0;
-      for (int idx = lane; idx < C * kMaxWarps; idx += 32) {
-        const int q = idx / kMaxWarps, w = idx % kMaxWarps;
-        if (w < nw) {
-          su += sm.slot_uk[(q * kMaxWarps + w) * 2 + 0];
-          sk += sm.slot_uk[(q * kMaxWarps + w) * 2 + 1];
+    forces_and_publish(true, overflow);
+    csync();  // B2
+    int st;
+    const SvrStep z = thermo ? sv[s % kNoiseChunk] : SvrStep{0.0, 0.0, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    const bool last = (s + 1 == B);
+    if (FP64) {
+      double su, sk;
+      totals_fp64(su, sk, st);
+      if (z.bad) st |= kStRngCap;
+      const double Un = 0.5 * su, Kn = 0.5 * sk;
+      // one lane forms the FP64 factor and K'; the CTA reads both after the
+      // barrier, so every thread takes the same decisions below
+      if (tid == 0) {
+        double alpha = 1.0, kp = Kn;
+        if (thermo) alpha = svr_alpha(Kn, K.kbar, K.nf, K.c_th, z.r1, z.s, &kp);
+        alpha_sh = alpha;
+        kp_sh = kp;
+      }
+      __syncthreads();
+      const double alpha = alpha_sh;
+      const double Kp = kp_sh;
+      if (!isfinite(alpha) || !isfinite(Un) || !isfinite(Kp)) st |= kStNumeric;
+      if (own) {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          v[j] *= alpha;
+          if (!last) v[j] += K.hdt * f[j];  // first half kick of the next step
         }
       }
-      su = warp_sum(su);
-      sk = warp_sum(sk);
-      if (lane == 0) {
-        const double Un = 0.5 * su, Kn = 0.5 * sk;
-        int st = 0;
-        for (int q = 0; q < C; ++q) st |= sm.slot_st[q];
-        double alpha = 1.0, Kp = Kn;
-        if (E.tau > 0.0) {
-          const double2 nz = sm.noise[s % T];
-          if (nz.y < 0.0) st |= kStRngCap;
-          alpha = svr_alpha(Kn, K.kbar, K.nf, K.c_th, nz.x, nz.y, &Kp);
+      U = Un;
+      Kin = Kp;
+      econs += Kn - Kp;
+    } else {
+      long long iu, ik;
+      totals_int(iu, ik, st);
+      if (z.bad) st |= kStRngCap;
+      // every warp forms alpha - 1 in FP32 from the same integer total
+      const float Kf = ll2f_split(ik) * (float)(0.5 * kEnUnit);
+      const float eps = thermo ? svr_eps(z, Kf) : 0.0f;
+      if (!isfinite(eps)) st |= kStNumeric;
+      if (own) {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const int d = q + j * P;
+          if (d >= 3) continue;
+          const float w = vf[j] + hf[j];
+          // second half kick + thermostat factor (+ next first half kick)
+          const float inc = fmaf(eps, w, last ? hf[j] : 2.0f * hf[j]);
+          vq[j] += f2ll_split(inc * kVelScale);
+          vf[j] = ll2f_split(vq[j]) * kVelUnit;
         }
-        if (!isfinite(Un) || !isfinite(Kp)) st |= kStNumeric;
-        sm.bcast[0] = Un;
-        sm.bcast[1] = Kp;
-        sm.bcast[2] = alpha;
-        sm.bcast[3] = Kn - Kp;
-        sm.bcast[4] = (double)st;
+      }
+      // FP64 bookkeeping of the stored energies, off the step's critical path:
+      // the step's (2K, alpha - 1) are recorded; warp 0 of CTA 0 folds the
+      // records into econs every kNoiseChunk steps and after the last step
+      if (crank == 0 && warp == 0) {
+        const int slot = s % kNoiseChunk;
+        if (lane == 0) {
+          sm.rec_k[slot] = ik;
+          sm.rec_e[slot] = eps;
+        }
+        if (slot == kNoiseChunk - 1 || last) {
+          __syncwarp();
+          double dsum = 0.0, kp = 0.0;
+          for (int t = lane; t <= slot; t += 32) {
+            const double Kn = 0.5 * (double)sm.rec_k[t] * kEnUnit;
+            const double a1 = 1.0 + (double)sm.rec_e[t];
+            dsum += Kn - Kn * a1 * a1;
+            if (t == slot) kp = Kn * a1 * a1;
+          }
+          econs += warp_sum(dsum);
+          kp = __shfl_sync(0xffffffffu, kp, slot & 31);
+          Kin = kp;
+          U = 0.5 * (double)iu * kEnUnit;
+          __syncwarp();
+        }
       }
     }
-    __syncthreads();
-    U = sm.bcast[0];
-    Kin = sm.bcast[1];
-    vs = sm.bcast[2];
-    econs += sm.bcast[3];
-    status = (int)sm.bcast[4];
+    status = st;
     ++done;
   }
-  // Apply the last thermostat factor so that the stored velocities are final.
-  if (vs != 1.0) {
-    for (int i = i0 + tid; i < i1; i += T) {
-      const int g = aoff + i;
-      S.vx[g] *= vs;
-      S.vy[g] *= vs;
-      S.vz[g] *= vs;
+  // write the state back
+  if (own) {
+#pragma unroll
+    for (int j = 0; j < ND; ++j) {
+      const int d = q + j * P;
+      if (d >= 3) continue;
+      qcomp(S, d)[g] = xq[j];
+      rcomp(S, d)[g] = ref[j];
+      if (FP64) {
+        vcomp(S, d)[g] = v[j];
+        fcomp(S, d)[g] = f[j];
+      } else {
+        vcomp(S, d)[g] = (double)vq[j] * 0x1.0p-48;
+        fcomp(S, d)[g] = (double)hf[j] / K.hdt;
+      }
     }
+    ncnt[(size_t)i * P + q] = cnt;
   }
   if (crank == 0 && tid == 0) {
     S.U[r] = U;
@@ -748,34 +1066,35 @@ __global__ void plain_rebuild(StateDev S, const EnsDev* __restrict__ ens,
   }
   if (!need) return;
   const int N = E.N;
-  Hi3* hp = reinterpret_cast<Hi3*>(sh);
+  uint4* spos = reinterpret_cast<uint4*>(sh);
+  Hi3* hp = reinterpret_cast<Hi3*>(spos + N);
   int* cstart = reinterpret_cast<int*>(hp + N);
   int* ccnt = cstart + (max_ncell + 1);
-  uint16_t* catoms = reinterpret_cast<uint16_t*>(ccnt + (max_ncell + 1));
-  uint16_t* acell = catoms + N;
+  uint16_t* acell = reinterpret_cast<uint16_t*>(ccnt + (max_ncell + 1));
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int g = rd.atom_off + i;
     hp[i] = Hi3{(uint32_t)(S.qx[g] >> 32), (uint32_t)(S.qy[g] >> 32), (uint32_t)(S.qz[g] >> 32)};
   }
   __syncthreads();
   auto hi_of = [&](int i) { return hp[i]; };
-  if (E.nc > 0) cta_build_cells(hi_of, N, E.nc, cstart, ccnt, catoms, acell, scr);
+  if (E.nc > 0) cta_build_cells(hi_of, N, E.nc, cstart, ccnt, spos, acell, scr);
   int overflow = 0;
   uint16_t* nb = S.nbr + rd.nbr_off;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int g = rd.atom_off + i;
-    S.ncnt[g] = build_atom_list(i, hi_of, N, E.nc, E.m, cstart, catoms, K.rl2u, nb, E.cap,
-                                &overflow);
+    S.ncnt[(size_t)rd.atom_off * 8 + i] = build_sublist<1>(i, 0, hi_of, N, E.nc, E.m, cstart,
+                                                           spos, K.rl2u, nb, E.capsub[0],
+                                                           &overflow);
     S.rx[g] = hp[i].x;
     S.ry[g] = hp[i].y;
     S.rz[g] = hp[i].z;
   }
-  if (overflow) atomicOr(&ovf, 1);
+  if (overflow) atomicOr(&ovf, overflow);
   __syncthreads();
   if (threadIdx.x == 0) {
-    S.valid[r] = ovf ? 0 : 1;
+    S.valid[r] = (ovf & kStOverflow) ? 0 : 1;
     S.nreb[r] += 1;
-    if (ovf) S.status[r] |= kStOverflow;
+    S.status[r] |= ovf;
   }
 }
 
@@ -792,7 +1111,7 @@ __global__ void plain_forces(StateDev S, const EnsDev* __restrict__ ens,
   if (i < E.N) {
     const int g = rd.atom_off + i;
     const uint64_t xi = S.qx[g], yi = S.qy[g], zi = S.qz[g];
-    const int cnt = S.ncnt[g];
+    const int cnt = S.ncnt[(size_t)rd.atom_off * 8 + i];
     const uint16_t* nb = S.nbr + rd.nbr_off;
     double fx = 0.0, fy = 0.0, fz = 0.0;
     for (int k = 0; k < cnt; ++k) {
@@ -1085,13 +1404,20 @@ size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64) {
   return batched_layout(max_n, max_ncell, threads, fp64, nullptr, nullptr);
 }
 
-cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
-                           const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
-                           const LaunchCfg& cfg, int max_n, int max_ncell, cudaStream_t st) {
-  if (n_work <= 0) return cudaSuccess;
-  const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, fp64);
-  const void* fn = fp64 ? (const void*)md_batched_kernel<true> : (const void*)md_batched_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <bool FP64, int P>
+static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                   const int* d_work, int n_work, const int32_t* d_budget,
+                                   const LaunchCfg& cfg, int max_n, int max_ncell,
+                                   cudaStream_t st) {
+  const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64);
+  cudaError_t e = cudaFuncSetAttribute(md_batched_kernel<FP64, P>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // shared memory for two CTAs per SM; the rest of the SM's 256 KB serves as L1
+  // (the neighbour lists are read from global memory every step)
+  const int carve = (int)std::min<size_t>(100, (2 * (smem + 1024) * 100 + 232447) / 232448);
+  e = cudaFuncSetAttribute(md_batched_kernel<FP64, P>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)(n_work * cfg.cluster));
@@ -1106,11 +1432,25 @@ cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev*
   lc.attrs = at;
   lc.numAttrs = 1;
   KernelDims dims{max_n, max_ncell};
-  if (fp64)
-    e = cudaLaunchKernelEx(&lc, md_batched_kernel<true>, s, d_ens, d_rep, d_work, d_budget, dims);
-  else
-    e = cudaLaunchKernelEx(&lc, md_batched_kernel<false>, s, d_ens, d_rep, d_work, d_budget, dims);
-  return e;
+  return cudaLaunchKernelEx(&lc, md_batched_kernel<FP64, P>, s, d_ens, d_rep, d_work, d_budget,
+                            dims);
+}
+
+cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                           const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
+                           const LaunchCfg& cfg, int max_n, int max_ncell, cudaStream_t st) {
+  if (n_work <= 0) return cudaSuccess;
+#define RE_LB(F, PP)                                                                           \
+  case PP:                                                                                     \
+    return launch_batched_t<F, PP>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg, max_n,     \
+                                   max_ncell, st);
+  if (fp64) {
+    switch (cfg.atom_threads) { RE_LB(true, 1) RE_LB(true, 2) RE_LB(true, 4) RE_LB(true, 8) }
+  } else {
+    switch (cfg.atom_threads) { RE_LB(false, 1) RE_LB(false, 2) RE_LB(false, 4) RE_LB(false, 8) }
+  }
+#undef RE_LB
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& rd, int r,
@@ -1122,7 +1462,7 @@ cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDe
   const int ncell = e.nc > 0 ? e.nc * e.nc * e.nc : 0;
   (void)max_ncell;
   (void)rd;
-  const size_t rsmem = (size_t)N * sizeof(Hi3) + (size_t)(ncell + 1) * 8 + (size_t)N * 4 + 64;
+  const size_t rsmem = (size_t)N * (16 + sizeof(Hi3)) + (size_t)(ncell + 1) * 8 + (size_t)N * 2 + 64;
   cudaError_t err = cudaFuncSetAttribute(plain_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rsmem);
   if (err != cudaSuccess) return err;

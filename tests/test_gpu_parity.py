@@ -59,7 +59,8 @@ def test_initial_state_matches_oracle(re, prec, N):
         _, Uo = O.forces_brute(O.fcc_lattice(N, L), L)
         tol = 1e-12 if prec == "fp64" else 1e-6
         assert abs(U[k] - Uo) <= tol * abs(Uo)
-        assert K[k] == pytest.approx(0.5 * (3 * N - 3) * t, rel=1e-12)
+        # mixed path: kinetic energy summed from FP32 squares (exact integer sum)
+        assert K[k] == pytest.approx(0.5 * (3 * N - 3) * t, rel=tol)
 
 
 @pytest.mark.parametrize("prec,ftol,utol", [("fp64", 1e-12, 1e-12), ("mixed", 1e-5, 1e-6)])
@@ -194,7 +195,7 @@ def test_graph_run_equals_eager(re):
 def test_uneven_group_matches_members(re):
     """Ensembles of 256, 500 and 864 atoms in one launch give the results each
     gives alone (same launch shape)."""
-    kw = dict(cluster=1, threads=128, cell_div=2)
+    kw = dict(cluster=2, atom_threads=2, cell_div=2)
     specs = [(256, 3, 0.7, 2.5), (500, 4, 0.7, 2.5), (864, 2, 0.7, 2.5)]
     alone, members = [], []
     for i, (N, R, t0, t1) in enumerate(specs):
