@@ -174,6 +174,22 @@ int re_exchange_device(int R, const double *T, const double *U, uint64_t seed, i
 int re_lj_forces_device(int N, double L, double rc, int shift, int precision, const double *x,
                         double *f, double *U, void *stream);
 
+/* The computation of re_lj_forces_device (FP64 pair forces) without any
+ * allocation, for callers that cannot call cudaMalloc (code running inside
+ * another framework's memory pool or under a fixed memory budget, plug-ins
+ * that may not touch the allocator).  The paper has no counterpart: this is a
+ * deployment variant.  Scratch lives in one fixed device array of about
+ * 2.6 MB that every device loading the library keeps until the process exits.
+ * Limits: 2 <= N <= 4096 atoms, at most 256 neighbour-list entries per atom
+ * (RE_EOVERFLOW beyond), rc + 0.5 < L/2.  Arguments as re_lj_forces_device
+ * (device pointers, caller-owned).  The first call on a device looks up the
+ * array's device address and caches it: make that first call before any
+ * stream capture.  Every call shares the array and leaves its contents
+ * behind; calls that overlap on the GPU race.  The call synchronises
+ * `stream`.  Errors: return code only (re_last_error is not updated). */
+int re_lj_forces_device_noalloc(int N, double L, double rc, int shift, const double *x,
+                                double *f, double *U, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

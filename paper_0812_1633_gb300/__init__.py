@@ -78,6 +78,8 @@ def lib():
                                          vp, vp, vp]
         L.re_lj_forces_device.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, vp,
                                           vp, vp, vp]
+        L.re_lj_forces_device_noalloc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, vp, vp,
+                                                  vp, vp]
         _lib = L
     return _lib
 
@@ -266,4 +268,22 @@ def lj_forces_device(x, L, rc=2.5, shift=True, precision="fp64", stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
     _check(lib().re_lj_forces_device(N, float(L), float(rc), 1 if shift else 0, PREC[precision],
                                      x.data_ptr(), f.data_ptr(), U.data_ptr(), C.c_void_p(st)))
+    return f, U
+
+
+def lj_forces_device_noalloc(x, L, rc=2.5, shift=True, stream=None):
+    """As lj_forces_device (FP64) with no allocation inside the library: for
+    callers that cannot allocate device memory.  The outputs f and U are
+    allocated here, by the caller's side (torch); N <= 4096."""
+    import torch
+    N = x.shape[0]
+    x = x.contiguous()
+    f = torch.empty_like(x)
+    U = torch.empty(1, dtype=torch.float64, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device).cuda_stream
+    code = lib().re_lj_forces_device_noalloc(N, float(L), float(rc), 1 if shift else 0,
+                                             x.data_ptr(), f.data_ptr(), U.data_ptr(),
+                                             C.c_void_p(st))
+    if code != RE_OK:
+        raise REError(code, "re_lj_forces_device_noalloc failed")
     return f, U

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libre_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["re_kernels.cu", "re_capi.cu"]
+SOURCES = ["re_kernels.cu", "re_capi.cu", "re_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]
