@@ -49,6 +49,7 @@ CONFIGS = {
 }
 FLOPS_PER_PAIR = 37.0   # unique pair: 34 for the pair itself + 3 for the reaction
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured FP64 peak is provided)
 
 
 def dist_env():
@@ -56,6 +57,28 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def rank_seed(rank):
+    """Each rank runs its own ensemble: a distinct seed per rank (weak scaling)."""
+    return 12345 + 1 + 1000 * rank
+
+
+def aggregate(total_s, work, ws, dist=None):
+    """Whole-job throughput: the slowest rank's time (max over ranks) and the
+    sum of the ranks' work (every rank runs the same workload)."""
+    if dist is not None and ws > 1:
+        import torch
+        t = torch.tensor([total_s], dtype=torch.float64)
+        w = torch.tensor([work], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t, w = t.cuda(), w.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        total_s, work = float(t.item()), float(w.item())
+    else:
+        work = work * ws
+    return total_s, work / total_s
 
 
 def make_budgets(cfg, R, cycles, seed):
@@ -256,7 +279,7 @@ def run_gpu(args, cfg):
     build.build()
     re.lib()
     desc, ens_spec, nx, skin, mode, prec = cfg
-    seed = 12345 + 1 + 1000 * rank
+    seed = rank_seed(rank)
     members = []
     for i, (N, R, t0, t1) in enumerate(ens_spec):
         L = inputs.box_length(N)
@@ -318,16 +341,12 @@ def run_gpu(args, cfg):
     adv_ms = [a.elapsed_time(b) for a, b, c in ev]
     exch_ms = [b.elapsed_time(c) for a, b, c in ev]
     total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
     work = sum(atoms_per_cycle(cfg, budgets[W + k]) for k in range(K))
-    value = ws * work / total_s
+    total_s, value = aggregate(total_s, work, ws, dist)
     n_ens = len(ens_spec)
     exch_per_s = ws * n_ens * K / total_s
-    pairs_per_attempt = sum((R - 1 - (a & 1)) // 2 + 1 if R > 1 else 0
-                            for (N, R, _, _) in ens_spec for a in range(2)) / 2
+    # pairs per attempt: (R - p) // 2 for first-pair offset p, alternating 0, 1
+    pairs_per_attempt = sum((R - p) // 2 for (N, R, _, _) in ens_spec for p in range(2)) / 2
 
     # ---- roofline of the dominant kernel (the batched MD launch)
     x, _ = ctx.get_state()
@@ -335,6 +354,7 @@ def run_gpu(args, cfg):
     adv_mean_s = statistics.mean(adv_ms) / 1e3
     flops_per_launch = FLOPS_PER_PAIR * pairs * work / K
     achieved = flops_per_launch / adv_mean_s / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
 
     # ---- e2e: public API with host buffers every step
     t_e2e0 = time.perf_counter()
@@ -392,9 +412,11 @@ def run_gpu(args, cfg):
             "exch_per_s": exch_per_s,
             "pair_attempts_per_s": exch_per_s * pairs_per_attempt / max(n_ens, 1),
             "advance_ms": statistics.mean(adv_ms), "exchange_ms": statistics.mean(exch_ms),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "md_batched_kernel<mixed>",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": f"md_batched_kernel<{prec}>",
+                         "peak_source": "FP64 nominal 1.25 TFLOP/s" if prec == "fp64" else
+                                        "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                          "algorithmic": f"{FLOPS_PER_PAIR:.0f} flop x {pairs:.2f} unique in-cutoff "
                                         f"pairs per atom-step"},
             "plain_fp64": plain,
@@ -411,6 +433,66 @@ def run_gpu(args, cfg):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ drift study
+def drift_slopes(times, H, N):
+    """Least-squares slope of H~/N against time (tau) for every replica."""
+    t = np.asarray(times)
+    Hn = np.asarray(H) / N
+    tc = t - t.mean()
+    return (tc[:, None] * (Hn - Hn.mean(0))).sum(0) / (tc * tc).sum()
+
+
+def run_drift(args):
+    """Energy drift of H~ = U + K + econs (per atom per tau) for the mixed and
+    FP64 batched paths, the plain FP64 path and the CPU oracle, on the same
+    seeded systems (256-replica precision workload reduced to R replicas)."""
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    build.build()
+    N, R = args.drift_n, args.drift_r
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.75, 1.8, R)
+    dt, chunk = 0.005, 100
+    out = {"study": "energy drift of H~ per atom per tau (least-squares slope)",
+           "workload": f"{R} replicas x {N} atoms, rho 0.8442, T 0.75-1.8, dt 0.005, tau_T 0.5, "
+                       f"FCC start, seed 12345",
+           "steps": args.drift_steps}
+    for name, kw in [("mixed_batched", dict(precision="mixed")),
+                     ("fp64_batched", dict(precision="fp64")),
+                     ("plain_fp64", dict(path="plain"))]:
+        steps = args.drift_steps if name != "plain_fp64" else min(args.drift_steps, 4000)
+        ctx = re.Context(N, L, 2.5, temps, 12345, **kw)
+        t, H = [], []
+        t0 = time.perf_counter()
+        for c in range(steps // chunk):
+            ctx.advance(chunk)
+            H.append(ctx.energies()[2])
+            t.append((c + 1) * chunk * dt)
+        wall = time.perf_counter() - t0
+        sl = drift_slopes(t, H, N)
+        common = min(len(t), args.drift_oracle_steps // chunk)
+        sc = drift_slopes(t[:common], H[:common], N)
+        out[name] = {"mean": float(sl.mean()), "max_abs": float(np.abs(sl).max()),
+                     "steps": steps, "replica_atom_steps_per_s": R * N * steps / wall,
+                     "common_window": {"steps": common * chunk, "mean": float(sc.mean()),
+                                       "max_abs": float(np.abs(sc).max())}}
+        ctx.close()
+    import oracle as O
+    ens = O.Ensemble(N, L, temps, 12345)
+    steps = min(args.drift_steps, args.drift_oracle_steps)
+    t, H = [], []
+    for c in range(steps // chunk):
+        ens.advance([chunk] * R)
+        H.append([r.H for r in ens.reps])
+        t.append((c + 1) * chunk * dt)
+    sl = drift_slopes(t, H, N)
+    out["oracle"] = {"mean": float(sl.mean()), "max_abs": float(np.abs(sl).max()), "steps": steps,
+                     "common_window": {"steps": steps, "mean": float(sl.mean()),
+                                       "max_abs": float(np.abs(sl).max())}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,12 +503,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--study", default=None, choices=["drift"],
+                    help="run a study instead of the throughput bench")
+    ap.add_argument("--drift-n", type=int, default=4000)
+    ap.add_argument("--drift-r", type=int, default=8)
+    ap.add_argument("--drift-steps", type=int, default=20000)
+    ap.add_argument("--drift-oracle-steps", type=int, default=4000)
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape 'cluster,atom_threads,cell_div' instead of the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     cfg = CONFIGS[args.config]
+    if args.study == "drift":
+        run_drift(args)
+        return
     if args.impl == "reference":
         run_reference(args, cfg)
     else:

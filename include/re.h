@@ -158,7 +158,7 @@ void re_destroy(re_ctx *c);
 /* One exchange attempt over R <= 4096 replicas (Implementation section), as
  * in re_exchange: T, U device arrays (R doubles); outputs T_out (R doubles,
  * new temperatures), partner (R int32, -1 if unpaired), accepted (R uint8),
- * vscale (R doubles, sqrt(T_new/T_old) or 1).  T must hold distinct values. */
+ * vscale (R doubles, sqrt(T_new/T_old) or 1).  T must hold distinct positive values. */
 int re_exchange_device(int R, const double *T, const double *U, uint64_t seed, int64_t attempt,
                        int parity_mode, double *T_out, int32_t *partner, uint8_t *accepted,
                        double *vscale, void *stream);

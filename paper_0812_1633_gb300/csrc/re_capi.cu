@@ -172,7 +172,10 @@ LaunchCfg default_cfg(const re_ctx* c) {
   const int sms = sm_count();
   int cl = c->opt.cluster;
   if (cl <= 0) {
+    // at least enough CTAs that one thread per atom fits in 1024 threads, then
+    // more until the replicas cover the SMs in about one wave
     cl = 1;
+    while (cl < 8 && (c->max_n + cl - 1) / cl > 1024) cl *= 2;
     while (cl < 8 && c->n_rep * cl < (sms * 4) / 5 && (c->max_n + 2 * cl - 1) / (2 * cl) >= 32)
       cl *= 2;
   }
@@ -251,6 +254,28 @@ void apply_cells(re_ctx* c, int want_m) {
   }
 }
 
+int max_smem_optin() {
+  int dev = 0, maxsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return maxsm > 0 ? maxsm : 232448;
+}
+
+// Shared-memory list entries per CTA for launch shape k: the largest CTA's
+// P sub-lists over all ensembles, or 0 when they would not fit (the kernel then
+// reads the lists from global memory).
+size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
+  const int pidx = k.atom_threads == 1 ? 0 : (k.atom_threads == 2 ? 1 : (k.atom_threads == 4 ? 2 : 3));
+  size_t elems = 0;
+  for (const auto& e : c->ens) {
+    const size_t per = (size_t)(e.N + k.cluster - 1) / k.cluster;
+    elems = std::max(elems, per * k.atom_threads * (size_t)e.capsub[pidx]);
+  }
+  const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
+                                             c->opt.precision == RE_PREC_FP64, elems);
+  return smem <= (size_t)max_smem_optin() ? elems : 0;
+}
+
 int check_cfg(re_ctx* c, const LaunchCfg& k) {
   if (k.cluster != 1 && k.cluster != 2 && k.cluster != 4 && k.cluster != 8)
     return fail(c, RE_EINVAL, "cluster must be 1, 2, 4 or 8 (got %d)", k.cluster);
@@ -260,11 +285,9 @@ int check_cfg(re_ctx* c, const LaunchCfg& k) {
     return fail(c, RE_EINVAL, "%d atoms per CTA x %d threads per atom exceed 1024 threads; "
                 "use more CTAs per replica", (c->max_n + k.cluster - 1) / k.cluster, k.atom_threads);
   const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
-                                             c->opt.precision == RE_PREC_FP64);
-  int dev = 0, maxsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (maxsm > 0 && smem > (size_t)maxsm)
+                                             c->opt.precision == RE_PREC_FP64, 0);
+  const int maxsm = max_smem_optin();
+  if (smem > (size_t)maxsm)
     return fail(c, RE_EINVAL, "replica of %d atoms needs %zu bytes of shared memory (max %d)",
                 c->max_n, smem, maxsm);
   return RE_OK;
@@ -274,7 +297,7 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget) 
   if (c->opt.path == RE_PATH_BATCHED) {
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
                                        c->opt.precision == RE_PREC_FP64, c->cfg, c->max_n,
-                                       c->max_ncell, c->stream);
+                                       c->max_ncell, list_elems_for(c, c->cfg), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
     return RE_OK;
   }

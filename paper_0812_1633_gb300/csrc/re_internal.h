@@ -64,10 +64,13 @@ void set_capacity(EnsDev& e, int user_cap);
 // Host-side launchers (re_kernels.cu).  All return the launch status.
 cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                 int n_rep, int max_threads, cudaStream_t st);
-size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64);
+size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size_t list_elems);
+// list_elems > 0: each CTA keeps its atoms' neighbour sub-lists (list_elems
+// uint16 entries) in shared memory during the launch
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
-                           const LaunchCfg& cfg, int max_n, int max_ncell, cudaStream_t st);
+                           const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
+                           cudaStream_t st);
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,
                                  const EnsDev* d_ens, const RepDev* d_rep, int steps,
                                  int max_ncell, cudaStream_t st, int refresh);

@@ -207,21 +207,26 @@ struct MixedAcc {
   int nin;
 };
 
+template <bool ENERGY, bool MAYBE_SELF>
 __device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, float rc2u, float inv_lam2,
                                            MixedAcc& a) {
   const float dx = (float)(int)(pj.x - pi.x);
   const float dy = (float)(int)(pj.y - pi.y);
   const float dz = (float)(int)(pj.z - pi.z);
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  if (r2 < rc2u && r2 > 0.0f) {  // r2 == 0: the atom itself (sub-list padding)
+  // r2 == 0 only for the atom itself (sub-list padding, last block only);
+  // distinct atoms at distance 0 are reported by the list build
+  if (r2 < rc2u && (!MAYBE_SELF || r2 > 0.0f)) {
     const float s = rcp_approx(r2) * inv_lam2;
     const float s3 = s * s * s;
     const float fs = (s * s3) * fmaf(-48.0f, s3, 24.0f);
     a.fx = fmaf(fs, dx, a.fx);
     a.fy = fmaf(fs, dy, a.fy);
     a.fz = fmaf(fs, dz, a.fz);
-    a.e = fmaf(s3, fmaf(4.0f, s3, -4.0f), a.e);
-    a.nin += 1;
+    if (ENERGY) {
+      a.e = fmaf(s3, fmaf(4.0f, s3, -4.0f), a.e);
+      a.nin += 1;
+    }
   }
 }
 
@@ -269,6 +274,7 @@ __device__ __forceinline__ StepConst step_const(const EnsDev& E, double T) {
 }
 
 struct BatchedSmem {
+  uint16_t* nb_sm;  // this CTA's neighbour sub-lists when they fit in shared memory
   void* pos;       // uint4[N] (mixed: top 32 bits of x, y, z) or Pos64[N] (fp64)
   int* cstart;     // ncell + 1
   int* ccnt;       // ncell
@@ -289,7 +295,8 @@ struct BatchedSmem {
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int threads, bool fp64,
-                                                 unsigned char* base, BatchedSmem* out) {
+                                                 size_t list_elems, unsigned char* base,
+                                                 BatchedSmem* out) {
   size_t off = 0;
   auto take = [&](size_t bytes, size_t al) {
     off = align_up(off, al);
@@ -297,6 +304,7 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
     off += bytes;
     return o;
   };
+  const size_t o_nbs = take(list_elems * 2, 16);
   const size_t o_pos = take((size_t)max_n * (fp64 ? 32 : 16), 32);
   const size_t o_sp = take((size_t)max_n * 16, 16);
   const size_t o_noise = take((size_t)kNoiseChunk * 2 * kSvrStepBytes, 16);
@@ -317,6 +325,7 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
   const size_t o_os = o_cn + (size_t)threads * 4;
   const size_t o_ac = o_un;
   if (out) {
+    out->nb_sm = reinterpret_cast<uint16_t*>(base + o_nbs);
     out->pos = base + o_pos;
     out->noise = reinterpret_cast<double2*>(base + o_noise);
     out->slot_uk = reinterpret_cast<double*>(base + o_uk);
@@ -338,6 +347,7 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
 
 struct KernelDims {
   int max_n, max_ncell;
+  size_t list_elems;  // shared-memory list entries per CTA (0: lists in global memory)
 };
 
 __device__ __forceinline__ uint64_t* qcomp(const StateDev& S, int d) {
@@ -356,13 +366,16 @@ __device__ __forceinline__ uint32_t* rcomp(const StateDev& S, int d) {
 // Sub-list of lane q (of P) of atom i: candidates of every scanned range are
 // dealt to the P lanes in turn (candidate k of a range goes to lane k % P).
 // Entry k of sub-list (i, q) sits at nb[((k/4) * N*P + i*P + q) * 4 + k%4].
+// The sub-list of column `col` of a list with `ncols` columns: entry k at
+// element ((k / 4) * ncols + col) * 4 + k % 4 of nb.
 template <int P, class PosFn>
 __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, const int* cstart,
-                             const uint4* spos, float rl2u, uint16_t* nb, int cap_sub,
-                             int* overflow) {
+                             const uint4* spos, float rl2u, uint16_t* nb, uint32_t col,
+                             uint32_t ncols, int cap_sub, int* overflow) {
   const Hi3 pi = pos_hi(i);
-  const size_t stride = (size_t)N * P;
-  const size_t col = (size_t)i * P + q;
+  // a running offset: +1 inside a block of four, + ncols*4 - 3 across blocks
+  uint32_t wofs = col * 4;
+  const uint32_t jump = ncols * 4 - 3u;
   int cnt = 0;
   auto accept = [&](int j, Hi3 pj) {
     const float r2 = sep2_hi(pi, pj);
@@ -370,7 +383,10 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
       // two distinct atoms at one point (closer than L / 2^32): the pair loop
       // treats distance 0 as the sub-list padding, so report it here
       if (r2 == 0.0f) *overflow |= kStNumeric;
-      if (cnt < cap_sub) nb[((size_t)(cnt >> 2) * stride + col) * 4 + (cnt & 3)] = (uint16_t)j;
+      if (cnt < cap_sub) {
+        nb[wofs] = (uint16_t)j;
+        wofs += ((cnt & 3) == 3) ? jump : 1u;
+      }
       ++cnt;
     }
   };
@@ -397,7 +413,16 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
         const int b1 = cstart[base + lo1], e1 = cstart[base + hi1];
         const int b2 = cstart[base], e2 = cstart[base + hi2];
         const int n1 = e1 - b1, n = n1 + (e2 - b2);
-        for (int t = q; t < n; t += P) {
+        // two candidates per iteration: both loads issue before either test
+        int t = q;
+        for (; t + P < n; t += 2 * P) {
+          const int t2 = t + P;
+          const uint4 v = spos[t < n1 ? b1 + t : b2 + (t - n1)];
+          const uint4 w = spos[t2 < n1 ? b1 + t2 : b2 + (t2 - n1)];
+          accept((int)v.w, Hi3{v.x, v.y, v.z});
+          accept((int)w.w, Hi3{w.x, w.y, w.z});
+        }
+        if (t < n) {
           const uint4 v = spos[t < n1 ? b1 + t : b2 + (t - n1)];
           accept((int)v.w, Hi3{v.x, v.y, v.z});
         }
@@ -409,48 +434,58 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
     cnt = cap_sub;
   }
   // pad to a whole block of four with the atom's own index (skipped by r2 > 0)
-  for (int k = cnt; k & 3; ++k) nb[((size_t)(k >> 2) * stride + col) * 4 + (k & 3)] = (uint16_t)i;
+  for (int k = cnt; k & 3; ++k) nb[wofs++] = (uint16_t)i;
   return cnt;
 }
 
 // Mixed-precision sub-list loop of lane (i, q); see mixed_pair.
-// Sub-lists are padded with the atom's own index up to a whole block of four,
-// so every block is processed without per-entry tests.
-template <int P>
-__device__ __forceinline__ MixedAcc mixed_sublist_forces(int i, int q, uint4 pi,
-                                                         const uint4* __restrict__ pos,
-                                                         const uint16_t* __restrict__ nb, int N,
-                                                         int cnt, float rc2u, float inv_lam2) {
+// Sub-lists are padded with the atom's own index up to a whole block of four;
+// only the last block can hold padding, so only it tests for the atom itself.
+// ENERGY: also sum the pair energies (needed only when U is reported).
+template <bool ENERGY>
+__device__ __forceinline__ MixedAcc mixed_sublist_forces(uint4 pi, const uint4* __restrict__ pos,
+                                                         const uint16_t* __restrict__ nb,
+                                                         uint32_t col, uint32_t ncols, int cnt,
+                                                         float rc2u, float inv_lam2) {
   MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
-  const size_t stride4 = (size_t)N * P * 4;
-  const uint16_t* base = nb + ((size_t)i * P + q) * 4;
+  const size_t stride4 = (size_t)ncols * 4;
+  const uint16_t* base = nb + (size_t)col * 4;
   const int nblk = (cnt + 3) >> 2;
+  const int nfull = cnt >> 2;
   uint2 w = nblk > 0 ? *reinterpret_cast<const uint2*>(base) : make_uint2(0u, 0u);
-  for (int kb = 0; kb < nblk; ++kb) {
+  for (int kb = 0; kb < nfull; ++kb) {
     // the next block of indices is requested before this block is used
     const uint2 wn = kb + 1 < nblk ? *reinterpret_cast<const uint2*>(base + (size_t)(kb + 1) * stride4) : w;
     const uint4 p0 = pos[w.x & 0xFFFFu];
     const uint4 p1 = pos[w.x >> 16];
     const uint4 p2 = pos[w.y & 0xFFFFu];
     const uint4 p3 = pos[w.y >> 16];
-    mixed_pair(pi, p0, rc2u, inv_lam2, a);
-    mixed_pair(pi, p1, rc2u, inv_lam2, a);
-    mixed_pair(pi, p2, rc2u, inv_lam2, a);
-    mixed_pair(pi, p3, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, false>(pi, p0, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, false>(pi, p1, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, false>(pi, p2, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, false>(pi, p3, rc2u, inv_lam2, a);
     w = wn;
+  }
+  if (nblk > nfull) {
+    const uint4 p0 = pos[w.x & 0xFFFFu];
+    const uint4 p1 = pos[w.x >> 16];
+    const uint4 p2 = pos[w.y & 0xFFFFu];
+    const uint4 p3 = pos[w.y >> 16];
+    mixed_pair<ENERGY, true>(pi, p0, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, true>(pi, p1, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, true>(pi, p2, rc2u, inv_lam2, a);
+    mixed_pair<ENERGY, true>(pi, p3, rc2u, inv_lam2, a);
   }
   return a;
 }
 
-template <int P>
-__device__ __forceinline__ void fp64_sublist_forces(int i, int q, Pos64 pi, const Pos64* pos,
-                                                    const uint16_t* nb, int N, int cnt,
+__device__ __forceinline__ void fp64_sublist_forces(Pos64 pi, const Pos64* pos, const uint16_t* nb,
+                                                    uint32_t col, uint32_t ncols, int cnt,
                                                     double lam64, double rc2, double uc,
                                                     double& fx, double& fy, double& fz,
                                                     double& e) {
   fx = fy = fz = e = 0.0;
-  const size_t stride = (size_t)N * P;
-  const size_t col = (size_t)i * P + q;
+  const size_t stride = ncols;
   for (int k = 0; k < cnt; ++k) {
     const int j = nb[((size_t)(k >> 2) * stride + col) * 4 + (k & 3)];
     const Pos64 pj = pos[j];
@@ -564,7 +599,7 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 // integers (exact, order independent).  The second half kick, the thermostat
 // factor and the next first half kick form one increment per coordinate.
 // FP64 path: FP64 state arithmetic and FP64 pair forces throughout.
-template <bool FP64, int P>
+template <bool FP64, int P, bool LSM>
 __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
                                                              const EnsDev* __restrict__ ens,
                                                              const RepDev* __restrict__ reps,
@@ -576,6 +611,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   __shared__ EnsDev E;
   __shared__ StepConst K;
   __shared__ double alpha_sh, kp_sh;
+  __shared__ float eps_sh;
+  __shared__ int st_sh;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
@@ -597,7 +634,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   BatchedSmem sm;
-  batched_layout(dims.max_n, dims.max_ncell, T, FP64, smem_raw, &sm);
+  batched_layout(dims.max_n, dims.max_ncell, T, FP64, dims.list_elems, smem_raw, &sm);
   uint4* posm = reinterpret_cast<uint4*>(sm.pos);
   Pos64* pos64 = reinterpret_cast<Pos64*>(sm.pos);
 
@@ -620,7 +657,12 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const bool own = i < i1;
   const int g = rd.atom_off + i;
   const int cap_sub = E.capsub[P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : 3))];
-  uint16_t* nb = S.nbr + rd.nbr_off;
+  uint16_t* nbg = S.nbr + rd.nbr_off;  // global lists: columns i * P + q of N * P
+  // lists used by the step loop: in shared memory (columns (i - i0) * P + q of
+  // per * P) when they fit, else the global ones
+  uint16_t* nb = LSM ? sm.nb_sm : nbg;
+  const uint32_t ncols = LSM ? (uint32_t)(per * P) : (uint32_t)(N * P);
+  const uint32_t mycol = LSM ? (uint32_t)((i - i0) * P + q) : (uint32_t)(i * P + q);
   int32_t* ncnt = S.ncnt + (size_t)rd.atom_off * 8;
   const float hl = (float)(K.hdt * K.lam32);  // FP32 half-kick factor per force unit
   const float dtqf = (float)K.dtq;
@@ -717,15 +759,16 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       if (gi < n_own) {
         // one CTA: every sorted slot is its own; several: the compacted slots
         const int a = (int)sm.spos[C == 1 ? gi : (int)sm.own_sorted[gi]].w;
+        const uint32_t col = LSM ? (uint32_t)((a - i0) * P + q) : (uint32_t)(a * P + q);
         const int c = build_sublist<P>(a, q, hi_of, N, E.nc, E.m, sm.cstart, sm.spos, K.rl2u, nb,
-                                       cap_sub, &overflow);
+                                       col, ncols, cap_sub, &overflow);
         sm.cnt_sh[(a - i0) * P + q] = c;
       }
       __syncthreads();
       if (own) cnt = sm.cnt_sh[(i - i0) * P + q];
     } else if (own) {
-      cnt = build_sublist<P>(i, q, hi_of, N, E.nc, E.m, sm.cstart, sm.spos, K.rl2u, nb, cap_sub,
-                             &overflow);
+      cnt = build_sublist<P>(i, q, hi_of, N, E.nc, E.m, sm.cstart, sm.spos, K.rl2u, nb, mycol,
+                             ncols, cap_sub, &overflow);
     }
     if (own) {
 #pragma unroll
@@ -737,15 +780,15 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // Forces on this lane's atom (sub-list sums combined over the P lanes) and
   // the second half kick when `kick`.  Publishes this warp's partial sums of
   // U and of v^2 (after the kick) to every CTA; returns the lanes' numeric flag.
-  auto forces_and_publish = [&](bool kick, int st_in) {
+  auto forces_and_publish = [&](bool kick, bool energy, int st_in) {
     int st = st_in;
     long long iu = 0, ik = 0;  // mixed: fixed-point partial sums
     double du = 0.0, dk = 0.0; // FP64 path
     if (FP64) {
       double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
       if (own)
-        fp64_sublist_forces<P>(i, q, pos64[i], pos64, nb, N, cnt, K.lam64, K.rc2, K.uc, fx, fy, fz,
-                               e);
+        fp64_sublist_forces(pos64[i], pos64, nb, mycol, ncols, cnt, K.lam64, K.rc2, K.uc, fx, fy,
+                            fz, e);
       fx = group_sum<P>(fx);
       fy = group_sum<P>(fy);
       fz = group_sum<P>(fz);
@@ -765,11 +808,18 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       dk = warp_sum(dk);
     } else {
       MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
-      if (own) a = mixed_sublist_forces<P>(i, q, posm[i], posm, nb, N, cnt, K.rc2u, K.inv_lam2);
-      const float ax = group_sum<P>(a.fx), ay = group_sum<P>(a.fy), az = group_sum<P>(a.fz);
-      const float ae = group_sum<P>(a.e) - ucf * (float)group_sum<P>(a.nin);
       if (own) {
-        if (q == 0) {
+        if (energy)
+          a = mixed_sublist_forces<true>(posm[i], posm, nb, mycol, ncols, cnt, K.rc2u, K.inv_lam2);
+        else
+          a = mixed_sublist_forces<false>(posm[i], posm, nb, mycol, ncols, cnt, K.rc2u, K.inv_lam2);
+      }
+      const float ax = group_sum<P>(a.fx), ay = group_sum<P>(a.fy), az = group_sum<P>(a.fz);
+      float ae = 0.0f;
+      if (energy) ae = group_sum<P>(a.e) - ucf * (float)group_sum<P>(a.nin);  // uniform flag
+      if (own) {
+        if (!isfinite(ax) || !isfinite(ay) || !isfinite(az)) st |= kStNumeric;
+        if (energy && q == 0) {
           if (!isfinite(ae)) st |= kStNumeric;
           iu = f2ll_split(ae * kEnScale);
         }
@@ -830,6 +880,18 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   };
 
   if (tid < C) sm.slot_st[tid] = 0;
+  // shared-memory lists: bring this CTA's valid lists in (blocks of four entries)
+  const int nblk_sub = cap_sub / 4;
+  if (LSM && valid0) {
+    const int cols = per * P;
+    for (int idx = tid; idx < nblk_sub * cols; idx += T) {
+      const int kb = idx / cols, c = idx - kb * cols;
+      if (i0 + c / P < i1)
+        reinterpret_cast<uint2*>(nb)[(size_t)kb * cols + c] =
+            reinterpret_cast<const uint2*>(nbg)[(size_t)kb * N * P + (size_t)i0 * P + c];
+    }
+    __syncthreads();
+  }
 
   double U = S.U[r], Kin = S.K[r];
   int status = 0;
@@ -839,7 +901,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     publish();
     csync();
     rebuild();
-    forces_and_publish(false, overflow);
+    forces_and_publish(false, true, overflow);
     csync();
     if (FP64) {
       double su, sk;
@@ -898,7 +960,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       if (idx % kMaxWarps < nw) mdall = fmaxf(mdall, sm.slot_md[idx]);
     mdall = warp_max(mdall);
     if (mdall > K.half2u) rebuild();
-    forces_and_publish(true, overflow);
+    // the pair energies are summed only when U is reported (the last step)
+    forces_and_publish(true, s + 1 == B, overflow);
     csync();  // B2
     int st;
     const SvrStep z = thermo ? sv[s % kNoiseChunk] : SvrStep{0.0, 0.0, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
@@ -931,13 +994,23 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       Kin = Kp;
       econs += Kn - Kp;
     } else {
-      long long iu, ik;
-      totals_int(iu, ik, st);
-      if (z.bad) st |= kStRngCap;
-      // every warp forms alpha - 1 in FP32 from the same integer total
-      const float Kf = ll2f_split(ik) * (float)(0.5 * kEnUnit);
-      const float eps = thermo ? svr_eps(z, Kf) : 0.0f;
-      if (!isfinite(eps)) st |= kStNumeric;
+      // warp 0 forms the integer totals and alpha - 1 (FP32); the block reads
+      // them after a block barrier (far cheaper than every warp repeating it)
+      long long iu = 0, ik = 0;
+      if (warp == 0) {
+        totals_int(iu, ik, st);
+        if (z.bad) st |= kStRngCap;
+        const float Kf = ll2f_split(ik) * (float)(0.5 * kEnUnit);
+        const float e0 = thermo ? svr_eps(z, Kf) : 0.0f;
+        if (!isfinite(e0)) st |= kStNumeric;
+        if (lane == 0) {
+          eps_sh = e0;
+          st_sh = st;
+        }
+      }
+      __syncthreads();
+      const float eps = eps_sh;
+      st = st_sh;
       if (own) {
 #pragma unroll
         for (int j = 0; j < ND; ++j) {
@@ -978,6 +1051,17 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     }
     status = st;
     ++done;
+  }
+  // shared-memory lists go back to global memory for the next launch
+  if (LSM) {
+    __syncthreads();
+    const int cols = per * P;
+    for (int idx = tid; idx < nblk_sub * cols; idx += T) {
+      const int kb = idx / cols, c = idx - kb * cols;
+      if (i0 + c / P < i1)
+        reinterpret_cast<uint2*>(nbg)[(size_t)kb * N * P + (size_t)i0 * P + c] =
+            reinterpret_cast<const uint2*>(nb)[(size_t)kb * cols + c];
+    }
   }
   // write the state back
   if (own) {
@@ -1082,9 +1166,9 @@ __global__ void plain_rebuild(StateDev S, const EnsDev* __restrict__ ens,
   uint16_t* nb = S.nbr + rd.nbr_off;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int g = rd.atom_off + i;
-    S.ncnt[(size_t)rd.atom_off * 8 + i] = build_sublist<1>(i, 0, hi_of, N, E.nc, E.m, cstart,
-                                                           spos, K.rl2u, nb, E.capsub[0],
-                                                           &overflow);
+    S.ncnt[(size_t)rd.atom_off * 8 + i] =
+        build_sublist<1>(i, 0, hi_of, N, E.nc, E.m, cstart, spos, K.rl2u, nb, (uint32_t)i,
+                         (uint32_t)N, E.capsub[0], &overflow);
     S.rx[g] = hp[i].x;
     S.ry[g] = hp[i].y;
     S.rz[g] = hp[i].z;
@@ -1221,13 +1305,17 @@ __device__ __forceinline__ int pair_offset(int mode, uint64_t seed, int64_t atte
 }
 
 // Sorted order of R distinct temperatures by counting (rank = number of
-// smaller values, ties broken by index).  Ts, order in shared memory.
+// smaller values, ties broken by index).  Ts, order in shared memory.  The
+// temperatures are positive, so their IEEE bit patterns read as 64-bit
+// integers order exactly like the values: the comparisons run on the integer
+// units instead of the (1/64-rate) FP64 unit.
 __device__ void rank_sort(const double* Ts, int* order, int R) {
+  const long long* key = reinterpret_cast<const long long*>(Ts);
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
-    const double t = Ts[a];
+    const long long t = key[a];
     int rank = 0;
     for (int b = 0; b < R; ++b) {
-      const double u = Ts[b];
+      const long long u = key[b];
       rank += (u < t) || (u == t && b < a);
     }
     order[rank] = a;
@@ -1400,24 +1488,25 @@ cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const Re
   return cudaGetLastError();
 }
 
-size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64) {
-  return batched_layout(max_n, max_ncell, threads, fp64, nullptr, nullptr);
+size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size_t list_elems) {
+  return batched_layout(max_n, max_ncell, threads, fp64, list_elems, nullptr, nullptr);
 }
 
-template <bool FP64, int P>
+template <bool FP64, int P, bool LSM>
 static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                    const int* d_work, int n_work, const int32_t* d_budget,
                                    const LaunchCfg& cfg, int max_n, int max_ncell,
-                                   cudaStream_t st) {
-  const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64);
-  cudaError_t e = cudaFuncSetAttribute(md_batched_kernel<FP64, P>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                   size_t list_elems, cudaStream_t st) {
+  const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
+  auto fn = md_batched_kernel<FP64, P, LSM>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // shared memory for two CTAs per SM; the rest of the SM's 256 KB serves as L1
-  // (the neighbour lists are read from global memory every step)
-  const int carve = (int)std::min<size_t>(100, (2 * (smem + 1024) * 100 + 232447) / 232448);
-  e = cudaFuncSetAttribute(md_batched_kernel<FP64, P>,
-                           cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+  // the rest of the SM's 256 KB serves as L1 (lists in global memory, state)
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, cfg.threads, smem);
+  per_sm = std::max(1, per_sm);
+  const int carve = (int)std::min<size_t>(100, (per_sm * (smem + 1024) * 100 + 232447) / 232448);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)(n_work * cfg.cluster));
@@ -1431,24 +1520,32 @@ static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, cons
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  KernelDims dims{max_n, max_ncell};
-  return cudaLaunchKernelEx(&lc, md_batched_kernel<FP64, P>, s, d_ens, d_rep, d_work, d_budget,
-                            dims);
+  KernelDims dims{max_n, max_ncell, list_elems};
+  return cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims);
 }
 
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
-                           const LaunchCfg& cfg, int max_n, int max_ncell, cudaStream_t st) {
+                           const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
+                           cudaStream_t st) {
   if (n_work <= 0) return cudaSuccess;
-#define RE_LB(F, PP)                                                                           \
-  case PP:                                                                                     \
-    return launch_batched_t<F, PP>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg, max_n,     \
-                                   max_ncell, st);
-  if (fp64) {
-    switch (cfg.atom_threads) { RE_LB(true, 1) RE_LB(true, 2) RE_LB(true, 4) RE_LB(true, 8) }
-  } else {
-    switch (cfg.atom_threads) { RE_LB(false, 1) RE_LB(false, 2) RE_LB(false, 4) RE_LB(false, 8) }
+  const bool lsm = list_elems > 0;
+#define RE_LB(F, PP, LS)                                                                      \
+  return launch_batched_t<F, PP, LS>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg, max_n,  \
+                                     max_ncell, list_elems, st);
+#define RE_LBP(F, LS)                              \
+  switch (cfg.atom_threads) {                      \
+    case 1: RE_LB(F, 1, LS)                        \
+    case 2: RE_LB(F, 2, LS)                        \
+    case 4: RE_LB(F, 4, LS)                        \
+    case 8: RE_LB(F, 8, LS)                        \
   }
+  if (fp64) {
+    if (lsm) { RE_LBP(true, true) } else { RE_LBP(true, false) }
+  } else {
+    if (lsm) { RE_LBP(false, true) } else { RE_LBP(false, false) }
+  }
+#undef RE_LBP
 #undef RE_LB
   return cudaErrorInvalidValue;
 }
