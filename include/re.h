@@ -75,6 +75,10 @@ typedef struct re_opts {
   int cell_div;     /* list cells per list radius (1..3); 0: automatic               */
   int cluster;      /* CTAs cooperating on one replica (1, 2, 4, 8); 0: automatic     */
   int atom_threads; /* threads sharing one atom's neighbour list (1, 2, 4, 8); 0: auto */
+  int sort_interval;/* mixed batched path: renumber each replica's atoms in space order
+                       every this many steps (0: every 200; < 0: never).  Results
+                       differ only in summation order; atom order in the API is
+                       always the original one. */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -101,6 +105,21 @@ int re_group(re_ctx *const *ctxs, int n, re_ctx **out);
  * kick, drift, list rebuild if some atom moved more than skin/2 since the
  * last rebuild, LJ forces, half kick, thermostat.  Asynchronous. */
 int re_advance(re_ctx *c, const int32_t *steps);
+
+/* Free-running (asynchronous) advance, the paper's scheme on one GPU
+ * (Implementation section): in every ensemble the master replica, which
+ * rotates with the attempt counter (replica attempt mod R), performs nx steps
+ * and then raises the ensemble's flag; every other replica checks the flag
+ * after each of its steps and stops after the step in which it sees it (and
+ * after at most 16 nx + 16 steps).  Replicas therefore do different numbers of
+ * steps between attempts (re_counters reports them).  Meaningful when all
+ * replicas of an ensemble run at once (replicas x cluster CTAs within the
+ * GPU's resident capacity); no thread ever waits on the flag.  Batched path
+ * only.  Asynchronous. */
+int re_advance_async(re_ctx *c, int nx);
+/* n_cycles times { re_advance_async(nx); re_exchange }, optionally as one
+ * CUDA graph. */
+int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
 
 /* One exchange attempt in every ensemble: temperatures sorted, sorted
  * neighbours paired from offset 0 or 1, Metropolis with the lower replica

@@ -33,7 +33,8 @@ class _Opts(C.Structure):
     _fields_ = [("dt", C.c_double), ("skin", C.c_double), ("tau_T", C.c_double),
                 ("shift_energy", C.c_int), ("precision", C.c_int), ("path", C.c_int),
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
-                ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int)]
+                ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int),
+                ("sort_interval", C.c_int)]
 
 
 _lib = None
@@ -57,6 +58,8 @@ def lib():
         L.re_advance.argtypes = [vp, i32p]
         L.re_exchange.argtypes = [vp, i32p, u8p]
         L.re_run.argtypes = [vp, C.c_int, i32p, C.c_int]
+        L.re_advance_async.argtypes = [vp, C.c_int]
+        L.re_run_async.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
@@ -106,7 +109,7 @@ class Context:
 
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
-                 cell_div=0, cluster=0, atom_threads=0, _handle=None):
+                 cell_div=0, cluster=0, atom_threads=0, sort_interval=0, _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -118,6 +121,7 @@ class Context:
             o.precision, o.path = PREC[precision], PATH[path]
             o.pair_parity, o.nx, o.nbr_capacity = pair_parity, nx, nbr_capacity
             o.cell_div, o.cluster, o.atom_threads = cell_div, cluster, atom_threads
+            o.sort_interval = sort_interval
             t = np.ascontiguousarray(temps, dtype=np.float64)
             _check(lib().re_create(int(N), float(L), float(rc), len(t), _p(t, C.c_double),
                                    int(seed) & (2**64 - 1), C.byref(o), C.byref(self._h)))
@@ -159,6 +163,14 @@ class Context:
             return
         s = np.ascontiguousarray(np.broadcast_to(np.asarray(steps, np.int32), (self.n_rep,)))
         _check(lib().re_advance(self._h, _p(s, C.c_int32)), self._h)
+
+    def advance_async(self, nx):
+        """Free-running advance: each ensemble's master (rotating) does nx steps,
+        the others stop at their next step boundary after it finishes."""
+        _check(lib().re_advance_async(self._h, int(nx)), self._h)
+
+    def run_async(self, cycles, nx, graph=True):
+        _check(lib().re_run_async(self._h, int(cycles), int(nx), 1 if graph else 0), self._h)
 
     def exchange(self, outputs=False):
         if not outputs:

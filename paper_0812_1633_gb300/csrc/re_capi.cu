@@ -108,6 +108,9 @@ struct re_ctx {
   uint8_t* d_acc = nullptr;
   double* d_io = nullptr;           // 3 * n_atoms doubles, state import/export
   bool plain_refresh = true;        // plain path: lists/forces need a prologue
+  int sort_every = 0;               // steps between spatial re-sorts (0: never)
+  int64_t since_sort = 0;           // steps (largest budget) since the last re-sort
+  bool tuning = false;              // autotune trials: no re-sorting
   std::vector<void*> allocs;
   std::string err;
   // cached graph of re_run
@@ -216,6 +219,9 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &s.attempt, E)) || (rc = dalloc(c, &s.pair_att, (size_t)c->n_pairs)) ||
       (rc = dalloc(c, &s.pair_acc, (size_t)c->n_pairs)) ||
       (rc = dalloc(c, &s.red, R * 1024)) || (rc = dalloc(c, &s.dmax, R)) ||
+      (rc = dalloc(c, &s.perm, A)) || (rc = dalloc(c, &s.order, A)) ||
+      (rc = dalloc(c, &s.stop, E)) ||
+      (rc = dalloc(c, &s.sbuf, 7 * A)) ||
       (rc = dalloc(c, &c->d_ens, E)) || (rc = dalloc(c, &c->d_rep, R)) ||
       (rc = dalloc(c, &c->d_work, R)) || (rc = dalloc(c, &c->d_budget, R)) ||
       (rc = dalloc(c, &c->d_budget_nx, R)) || (rc = dalloc(c, &c->d_partner, R)) ||
@@ -242,7 +248,12 @@ int allocate(re_ctx* c) {
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget_nx, nx.data(), sizeof(int32_t) * R,
                              cudaMemcpyHostToDevice, c->stream), "upload nx");
   RE_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
-  return upload_tables(c);
+  int rc2 = upload_tables(c);
+  if (rc2) return rc2;
+  // every context starts with its atoms in original order
+  cudaError_t e = re::launch_identity_perm(c->s, c->d_ens, c->d_rep, c->n_rep, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "identity permutation");
+  return RE_OK;
 }
 
 // Fill per-ensemble cells for the current cfg.cell_div; returns max ncell.
@@ -293,11 +304,26 @@ int check_cfg(re_ctx* c, const LaunchCfg& k) {
   return RE_OK;
 }
 
-int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget) {
+int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
+                   int max_budget = -1, int async_nx = 0) {
   if (c->opt.path == RE_PATH_BATCHED) {
+    // renumber atoms in space order every sort_every steps (mixed path): warps
+    // then hold neighbouring atoms, whose lists and gathers overlap
+    if (c->sort_every > 0 && !c->tuning && c->since_sort >= c->sort_every) {
+      cudaError_t e = re::launch_spatial_sort(c->s, c->d_ens, c->d_rep, c->n_rep, c->max_n,
+                                              c->max_ncell, c->n_atoms, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "spatial sort");
+      c->since_sort = 0;
+    }
+    c->since_sort += max_budget >= 0 ? max_budget : c->opt.nx;
+    if (async_nx > 0) {
+      cudaError_t e = cudaMemsetAsync(c->s.stop, 0, sizeof(int32_t) * c->ens.size(), c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "clear stop flags");
+    }
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
                                        c->opt.precision == RE_PREC_FP64, c->cfg, c->max_n,
-                                       c->max_ncell, list_elems_for(c, c->cfg), c->stream);
+                                       c->max_ncell, list_elems_for(c, c->cfg), async_nx,
+                                       c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
     return RE_OK;
   }
@@ -319,7 +345,7 @@ int refresh(re_ctx* c) {
   if (c->opt.path == RE_PATH_BATCHED) {
     // budget 0 with invalid lists: the kernel's prologue builds lists, forces, U, K
     RE_CUDA(c, cudaMemsetAsync(c->d_budget, 0, sizeof(int32_t) * c->n_rep, c->stream), "memset");
-    return launch_advance(c, c->d_budget, nullptr);
+    return launch_advance(c, c->d_budget, nullptr, 0);
   }
   c->plain_refresh = true;
   std::vector<int32_t> zero(c->n_rep, 0);
@@ -384,6 +410,10 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
   if (atom_off > INT32_MAX) return fail(c, RE_EINVAL, "too many atoms in one context");
   c->n_rep = rep_off;
   c->n_pairs = pair_off;
+  c->sort_every = (c->opt.path == RE_PATH_BATCHED && c->opt.precision == RE_PREC_MIXED &&
+                   c->opt.sort_interval >= 0)
+                      ? (c->opt.sort_interval > 0 ? c->opt.sort_interval : 200)
+                      : 0;
   c->n_atoms = atom_off;
   c->n_nbr = nbr_off;
   apply_cells(c, c->opt.cell_div);
@@ -415,6 +445,7 @@ void re_default_opts(re_opts* o) {
   o->cell_div = 0;
   o->cluster = 0;
   o->atom_threads = 0;
+  o->sort_interval = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -532,6 +563,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
     cp(c->s.vx + a0, s->s.vx, 8 * A);
     cp(c->s.vy + a0, s->s.vy, 8 * A);
     cp(c->s.vz + a0, s->s.vz, 8 * A);
+    cp(c->s.perm + a0, s->s.perm, 4 * A);
     cp(c->s.fx + a0, s->s.fx, 8 * A);
     cp(c->s.fy + a0, s->s.fy, 8 * A);
     cp(c->s.fz + a0, s->s.fz, 8 * A);
@@ -566,7 +598,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
 
 int re_advance(re_ctx* c, const int32_t* steps) {
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
-  if (!steps) return launch_advance(c, c->d_budget_nx, nullptr);
+  if (!steps) return launch_advance(c, c->d_budget_nx, nullptr, c->opt.nx);
   for (int r = 0; r < c->n_rep; ++r)
     if (steps[r] < 0) return fail(c, RE_EINVAL, "steps[%d] is negative", r);
   if (c->opt.path == RE_PATH_PLAIN) return launch_advance(c, nullptr, steps);
@@ -579,7 +611,64 @@ int re_advance(re_ctx* c, const int32_t* steps) {
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget, h, sizeof(int32_t) * c->n_rep, cudaMemcpyHostToDevice,
                              c->stream), "upload budgets");
   RE_CUDA(c, cudaEventRecord(c->ring_ev[slot], c->stream), "ring record");
-  return launch_advance(c, c->d_budget, nullptr);
+  int mx = 0;
+  for (int r = 0; r < c->n_rep; ++r) mx = std::max(mx, (int)steps[r]);
+  return launch_advance(c, c->d_budget, nullptr, mx);
+}
+
+int re_advance_async(re_ctx* c, int nx) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (nx < 1) return fail(c, RE_EINVAL, "nx must be >= 1");
+  if (c->opt.path != RE_PATH_BATCHED)
+    return fail(c, RE_EINVAL, "free-running mode needs the batched path");
+  // the cap of the non-master replicas bounds the host's step bookkeeping
+  return launch_advance(c, c->d_budget_nx, nullptr, nx, nx);
+}
+
+int re_run_async(re_ctx* c, int n_cycles, int nx, int use_graph) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (n_cycles < 0 || nx < 1) return fail(c, RE_EINVAL, "n_cycles >= 0 and nx >= 1 required");
+  if (c->opt.path != RE_PATH_BATCHED)
+    return fail(c, RE_EINVAL, "free-running mode needs the batched path");
+  auto enqueue = [&]() -> int {
+    for (int k = 0; k < n_cycles; ++k) {
+      int rc = launch_advance(c, c->d_budget_nx, nullptr, nx, nx);
+      if (rc) return rc;
+      cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
+                                          c->d_partner, c->d_acc, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+    }
+    return RE_OK;
+  };
+  if (!use_graph || n_cycles == 0) return enqueue();
+  cudaStream_t cap = nullptr;
+  RE_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
+  cudaStream_t saved = c->stream;
+  c->stream = cap;
+  cudaGraph_t g = nullptr;
+  int rc = RE_OK;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue();
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    if (rc == RE_OK && e2 != cudaSuccess) rc = cuda_fail(c, e2, "graph capture");
+  } else {
+    rc = cuda_fail(c, e, "begin capture");
+  }
+  c->stream = saved;
+  cudaStreamDestroy(cap);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  e = cudaGraphLaunch(ge, c->stream);
+  cudaGraphExecDestroy(ge);  // released once the launch completes
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  return RE_OK;
 }
 
 int re_exchange(re_ctx* c, int32_t* partner_out, uint8_t* accepted_out) {
@@ -639,7 +728,12 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
   }
   auto enqueue = [&]() -> int {
     for (int k = 0; k < n_cycles; ++k) {
-      int rc = launch_advance(c, dbud + stride * k, nullptr);
+      int mx = c->opt.nx;
+      if (steps) {
+        mx = 0;
+        for (int r = 0; r < c->n_rep; ++r) mx = std::max(mx, (int)steps[(size_t)k * c->n_rep + r]);
+      }
+      int rc = launch_advance(c, dbud + stride * k, nullptr, mx);
       if (rc) return rc;
       cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
                                           c->d_partner, c->d_acc, c->stream);
@@ -840,6 +934,7 @@ int re_autotune(re_ctx* c, int steps) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  c->tuning = true;
   const LaunchCfg keep = c->cfg;
   const int keep_m = c->ens[0].m;
   LaunchCfg best = keep;
@@ -903,6 +998,7 @@ int re_autotune(re_ctx* c, int steps) {
   }
   cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
   cudaStreamSynchronize(c->stream);
+  c->tuning = false;
   for (auto& b : bufs) cudaFree(b.save);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -20,7 +20,7 @@
 
 namespace re {
 
-enum StatusBits : int { kStOverflow = 1, kStNumeric = 2, kStRngCap = 4 };
+enum StatusBits : int { kStOverflow = 1, kStNumeric = 2, kStRngCap = 4, kStStop = 8 /* not an error */ };
 
 struct EnsDev {
   int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
@@ -50,6 +50,11 @@ struct StateDev {
   int64_t *pair_att, *pair_acc;      // per ensemble pair position
   double* red;                       // plain path: per replica reduction scratch
   uint32_t* dmax;                    // plain path: per replica max displacement^2 (float bits)
+  int32_t* stop;                     // per ensemble: free-running mode, the master's "done" flag
+  int32_t* perm;                     // per atom: original index (within its replica) of the
+                                     // atom held in this slot (atoms are renumbered in space order)
+  int32_t* order;                    // per atom: spatial re-sort order (scratch)
+  uint64_t* sbuf;                    // 7 words per atom: re-sort staging (scratch)
 };
 
 struct LaunchCfg {
@@ -67,10 +72,13 @@ cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const Re
 size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size_t list_elems);
 // list_elems > 0: each CTA keeps its atoms' neighbour sub-lists (list_elems
 // uint16 entries) in shared memory during the launch
+// async_nx > 0: free-running mode (budgets ignored): in every ensemble the
+// master replica (attempt mod R) does async_nx steps and then raises the
+// ensemble's stop flag; the others stop after the step in which they see it.
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
                            const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
-                           cudaStream_t st);
+                           int async_nx, cudaStream_t st);
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,
                                  const EnsDev* d_ens, const RepDev* d_rep, int steps,
                                  int max_ncell, cudaStream_t st, int refresh);
@@ -83,6 +91,14 @@ cudaError_t launch_export_state(const StateDev& s, const EnsDev* d_ens, const Re
                                 cudaStream_t st);
 cudaError_t launch_import_state(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                 int n_rep, const double* d_x, const double* d_v,
+                                cudaStream_t st);
+// perm = identity for every replica (every context starts in original order)
+cudaError_t launch_identity_perm(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                 int n_rep, cudaStream_t st);
+// Renumber the atoms of every replica in cell order (state permuted, lists
+// invalidated); getters and setters map slots back through perm.
+cudaError_t launch_spatial_sort(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                int n_rep, int max_n, int max_ncell, int64_t n_atoms,
                                 cudaStream_t st);
 cudaError_t launch_exchange_raw(int R, const double* T, const double* U, uint64_t seed,
                                 int64_t attempt, int parity_mode, double* T_out,

@@ -59,6 +59,7 @@ __global__ void init_lattice_kernel(StateDev S, const EnsDev* __restrict__ ens,
     const double x = (ix + bx[b] + 0.25) * a, y = (iy + by[b] + 0.25) * a,
                  z = (iz + bz[b] + 0.25) * a;
     const int g = rd.atom_off + i;
+    S.perm[g] = i;
     S.qx[g] = fix_from_double(x, inv_l);
     S.qy[g] = fix_from_double(y, inv_l);
     S.qz[g] = fix_from_double(z, inv_l);
@@ -348,7 +349,11 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
 struct KernelDims {
   int max_n, max_ncell;
   size_t list_elems;  // shared-memory list entries per CTA (0: lists in global memory)
+  int async_nx;       // > 0: free-running mode with this many master steps
 };
+
+// free-running mode: step cap of the non-master replicas (a bound, not a budget)
+constexpr int kAsyncCapFactor = 16;
 
 __device__ __forceinline__ uint64_t* qcomp(const StateDev& S, int d) {
   return d == 0 ? S.qx : (d == 1 ? S.qy : S.qz);
@@ -625,7 +630,21 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const int T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nw = (T + 31) >> 5;
   const int q = tid & (P - 1);
-  const int B = budget[r];
+  // Budget mode: budget[r] steps.  Free-running mode (Implementation section):
+  // the ensemble's master (replica attempt mod R, rotating with every attempt)
+  // does async_nx steps and then raises the ensemble's stop flag; every other
+  // replica checks the flag after each step and stops after the step in which
+  // it sees it (at most kAsyncCapFactor * async_nx + 16 steps).  No thread waits.
+  const int async_nx = dims.async_nx;
+  bool is_master = false;
+  int B;
+  if (async_nx > 0) {
+    const int Rens = ens[rd.ens].R;
+    is_master = rd.id == (int)(S.attempt[rd.ens] % Rens);
+    B = is_master ? async_nx : kAsyncCapFactor * async_nx + 16;
+  } else {
+    B = budget[r];
+  }
   const int status0 = S.status[r];
   const int valid0 = S.valid[r];
   const double vs0 = S.vscale[r];
@@ -960,12 +979,21 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       if (idx % kMaxWarps < nw) mdall = fmaxf(mdall, sm.slot_md[idx]);
     mdall = warp_max(mdall);
     if (mdall > K.half2u) rebuild();
-    // the pair energies are summed only when U is reported (the last step)
-    forces_and_publish(true, s + 1 == B, overflow);
+    // the pair energies are summed only when U is reported (the last step;
+    // every step in free-running mode, where the last step is not known ahead)
+    forces_and_publish(true, async_nx > 0 || s + 1 == B, overflow);
+    // free-running mode: CTA 0 reads the master's flag and tells every CTA of
+    // the cluster (through the status slots) that this step is the last
+    if (async_nx > 0 && !is_master && crank == 0 && tid == 0) {
+      if (*reinterpret_cast<volatile int32_t*>(S.stop + rd.ens))
+        for (int rk = 0; rk < C; ++rk) atomicOr(cl.map_shared_rank(sm.slot_st, rk), (int)kStStop);
+    }
     csync();  // B2
     int st;
     const SvrStep z = thermo ? sv[s % kNoiseChunk] : SvrStep{0.0, 0.0, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-    const bool last = (s + 1 == B);
+    // the stop bit is in every CTA's slots after B2: read it before the update
+    const bool stop_seen = (sm.slot_st[0] & kStStop) != 0;
+    const bool last = (s + 1 == B) || stop_seen;
     if (FP64) {
       double su, sk;
       totals_fp64(su, sk, st);
@@ -1051,6 +1079,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     }
     status = st;
     ++done;
+    // the master, having finished its steps, raises the ensemble's stop flag
+    if (is_master && s + 1 == B && crank == 0 && tid == 0) {
+      __threadfence();
+      atomicExch(S.stop + rd.ens, 1);
+    }
   }
   // shared-memory lists go back to global memory for the next launch
   if (LSM) {
@@ -1088,7 +1121,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     S.step[r] = step0 + done;
     S.nreb[r] += nreb;
     S.vscale[r] = 1.0;
-    S.status[r] = status;
+    S.status[r] = status & ~kStStop;
     S.valid[r] = (status & kStOverflow) ? 0 : 1;
   }
   cl.sync();  // no CTA leaves while another may still touch its shared memory
@@ -1431,23 +1464,25 @@ __global__ void export_kernel(StateDev S, const EnsDev* __restrict__ ens,
   const EnsDev E = ens[rd.ens];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E.N; i += gridDim.x * blockDim.x) {
     const int g = rd.atom_off + i;
+    // original order (no permutation array: slots are the original order)
+    const size_t o = (size_t)rd.atom_off + (S.perm ? S.perm[g] : i);
     if (x) {
       const uint64_t q[3] = {S.qx[g], S.qy[g], S.qz[g]};
       for (int d = 0; d < 3; ++d) {
         double xv = fix_to_double(q[d], E.L);
         if (xv >= E.L) xv -= E.L;  // rounding of a word just below 2^64
-        x[3 * (size_t)g + d] = xv;
+        x[3 * o + d] = xv;
       }
     }
     if (v) {
-      v[3 * (size_t)g + 0] = S.vx[g];
-      v[3 * (size_t)g + 1] = S.vy[g];
-      v[3 * (size_t)g + 2] = S.vz[g];
+      v[3 * o + 0] = S.vx[g];
+      v[3 * o + 1] = S.vy[g];
+      v[3 * o + 2] = S.vz[g];
     }
     if (f) {
-      f[3 * (size_t)g + 0] = S.fx[g];
-      f[3 * (size_t)g + 1] = S.fy[g];
-      f[3 * (size_t)g + 2] = S.fz[g];
+      f[3 * o + 0] = S.fx[g];
+      f[3 * o + 1] = S.fy[g];
+      f[3 * o + 2] = S.fz[g];
     }
   }
 }
@@ -1460,15 +1495,17 @@ __global__ void import_kernel(StateDev S, const EnsDev* __restrict__ ens,
   const double inv_l = 1.0 / E.L;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < E.N; i += gridDim.x * blockDim.x) {
     const int g = rd.atom_off + i;
+    // original order (no permutation array: slots are the original order)
+    const size_t o = (size_t)rd.atom_off + (S.perm ? S.perm[g] : i);
     if (x) {
-      S.qx[g] = fix_from_double(x[3 * (size_t)g + 0], inv_l);
-      S.qy[g] = fix_from_double(x[3 * (size_t)g + 1], inv_l);
-      S.qz[g] = fix_from_double(x[3 * (size_t)g + 2], inv_l);
+      S.qx[g] = fix_from_double(x[3 * o + 0], inv_l);
+      S.qy[g] = fix_from_double(x[3 * o + 1], inv_l);
+      S.qz[g] = fix_from_double(x[3 * o + 2], inv_l);
     }
     if (v) {
-      S.vx[g] = v[3 * (size_t)g + 0];
-      S.vy[g] = v[3 * (size_t)g + 1];
-      S.vz[g] = v[3 * (size_t)g + 2];
+      S.vx[g] = v[3 * o + 0];
+      S.vy[g] = v[3 * o + 1];
+      S.vz[g] = v[3 * o + 2];
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1476,6 +1513,72 @@ __global__ void import_kernel(StateDev S, const EnsDev* __restrict__ ens,
     S.vscale[r] = 1.0;
     S.status[r] = 0;
   }
+}
+
+// ------------------------------------------------------------------ spatial sort
+// Order of the atoms of one replica by cell (the list cells, or 4 per side
+// when the replica has none), ties by current slot: the same counting sort as
+// the list build.  One CTA per replica.
+__global__ void sort_order_kernel(StateDev S, const EnsDev* __restrict__ ens,
+                                  const RepDev* __restrict__ reps, int max_ncell) {
+  extern __shared__ __align__(16) unsigned char sh[];
+  __shared__ int scr[64];
+  const int r = blockIdx.x;
+  const RepDev rd = reps[r];
+  const EnsDev E = ens[rd.ens];
+  const int N = E.N;
+  const int nc = E.nc > 0 ? E.nc : 4;
+  uint4* spos = reinterpret_cast<uint4*>(sh);
+  Hi3* hp = reinterpret_cast<Hi3*>(spos + N);
+  int* cstart = reinterpret_cast<int*>(hp + N);
+  int* ccnt = cstart + (max_ncell + 1);
+  uint16_t* acell = reinterpret_cast<uint16_t*>(ccnt + (max_ncell + 1));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int g = rd.atom_off + i;
+    hp[i] = Hi3{(uint32_t)(S.qx[g] >> 32), (uint32_t)(S.qy[g] >> 32), (uint32_t)(S.qz[g] >> 32)};
+  }
+  __syncthreads();
+  auto hi_of = [&](int i) { return hp[i]; };
+  cta_build_cells(hi_of, N, nc, cstart, ccnt, spos, acell, scr);
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    S.order[rd.atom_off + k] = rd.atom_off + (int)spos[k].w;
+}
+
+__global__ void identity_perm_kernel(StateDev S, const EnsDev* __restrict__ ens,
+                                     const RepDev* __restrict__ reps) {
+  const int r = blockIdx.y;
+  const RepDev rd = reps[r];
+  const int N = ens[rd.ens].N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    S.perm[rd.atom_off + i] = i;
+}
+
+// staging copy in the new order: positions, velocities, permutation
+__global__ void sort_gather_kernel(StateDev S, int64_t n_atoms) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_atoms) return;
+  const int src = S.order[g];
+  S.sbuf[7 * g + 0] = S.qx[src];
+  S.sbuf[7 * g + 1] = S.qy[src];
+  S.sbuf[7 * g + 2] = S.qz[src];
+  S.sbuf[7 * g + 3] = (uint64_t)__double_as_longlong(S.vx[src]);
+  S.sbuf[7 * g + 4] = (uint64_t)__double_as_longlong(S.vy[src]);
+  S.sbuf[7 * g + 5] = (uint64_t)__double_as_longlong(S.vz[src]);
+  S.sbuf[7 * g + 6] = (uint64_t)(uint32_t)S.perm[src];
+}
+
+__global__ void sort_scatter_kernel(StateDev S, int64_t n_atoms, int n_rep) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n_atoms) {
+    S.qx[g] = S.sbuf[7 * g + 0];
+    S.qy[g] = S.sbuf[7 * g + 1];
+    S.qz[g] = S.sbuf[7 * g + 2];
+    S.vx[g] = __longlong_as_double((long long)S.sbuf[7 * g + 3]);
+    S.vy[g] = __longlong_as_double((long long)S.sbuf[7 * g + 4]);
+    S.vz[g] = __longlong_as_double((long long)S.sbuf[7 * g + 5]);
+    S.perm[g] = (int32_t)(uint32_t)S.sbuf[7 * g + 6];
+  }
+  if (g < n_rep) S.valid[g] = 0;  // lists and forces are rebuilt by the next launch
 }
 
 }  // namespace
@@ -1496,7 +1599,7 @@ template <bool FP64, int P, bool LSM>
 static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                    const int* d_work, int n_work, const int32_t* d_budget,
                                    const LaunchCfg& cfg, int max_n, int max_ncell,
-                                   size_t list_elems, cudaStream_t st) {
+                                   size_t list_elems, int async_nx, cudaStream_t st) {
   const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
   auto fn = md_batched_kernel<FP64, P, LSM>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1520,19 +1623,19 @@ static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, cons
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  KernelDims dims{max_n, max_ncell, list_elems};
+  KernelDims dims{max_n, max_ncell, list_elems, async_nx};
   return cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims);
 }
 
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
                            const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
-                           cudaStream_t st) {
+                           int async_nx, cudaStream_t st) {
   if (n_work <= 0) return cudaSuccess;
   const bool lsm = list_elems > 0;
 #define RE_LB(F, PP, LS)                                                                      \
   return launch_batched_t<F, PP, LS>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg, max_n,  \
-                                     max_ncell, list_elems, st);
+                                     max_ncell, list_elems, async_nx, st);
 #define RE_LBP(F, LS)                              \
   switch (cfg.atom_threads) {                      \
     case 1: RE_LB(F, 1, LS)                        \
@@ -1615,6 +1718,30 @@ cudaError_t launch_import_state(const StateDev& s, const EnsDev* d_ens, const Re
                                 cudaStream_t st) {
   if (n_rep <= 0) return cudaSuccess;
   import_kernel<<<dim3(32, n_rep), 256, 0, st>>>(s, d_ens, d_rep, d_x, d_v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_identity_perm(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                 int n_rep, cudaStream_t st) {
+  if (n_rep <= 0 || !s.perm) return cudaSuccess;
+  identity_perm_kernel<<<dim3(16, n_rep), 256, 0, st>>>(s, d_ens, d_rep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spatial_sort(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
+                                int n_rep, int max_n, int max_ncell, int64_t n_atoms,
+                                cudaStream_t st) {
+  if (n_rep <= 0) return cudaSuccess;
+  const int mc = std::max(max_ncell, 64);
+  const size_t smem = (size_t)max_n * (16 + sizeof(Hi3)) + (size_t)(mc + 1) * 8 +
+                      (size_t)max_n * 2 + 64;
+  cudaError_t e = cudaFuncSetAttribute(sort_order_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  sort_order_kernel<<<n_rep, 1024, smem, st>>>(s, d_ens, d_rep, mc);
+  const int nb = (int)((n_atoms + 255) / 256);
+  sort_gather_kernel<<<nb, 256, 0, st>>>(s, n_atoms);
+  sort_scatter_kernel<<<std::max(nb, (n_rep + 255) / 256), 256, 0, st>>>(s, n_atoms, n_rep);
   return cudaGetLastError();
 }
 

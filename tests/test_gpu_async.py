@@ -1,0 +1,104 @@
+"""Free-running (asynchronous) mode of the batched kernel (Implementation section).
+
+The master replica of each ensemble (replica attempt mod R) performs exactly
+N_x steps; every other replica stops at the first step boundary after the
+master has finished.  The number of steps a replica makes is thus decided by
+timing, but its trajectory is not: given the step counts the GPU reports, the
+FP64 oracle run for those counts must land on the same states (the stop rule
+only chooses where the velocity-Verlet / thermostat sequence ends).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0812_1633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def re():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0812_1633_gb300 import build
+    build.build()
+    import paper_0812_1633_gb300 as m
+    m.lib()
+    return m
+
+
+def compare(ctx, ens, N, L, tol=1e-10):
+    x, v = ctx.get_state()
+    U, K, H = ctx.energies()
+    for k, r in enumerate(ens.reps):
+        d = x[k * N:(k + 1) * N] - r.x
+        d -= L * np.rint(d / L)
+        assert np.abs(d).max() < tol, k
+        assert np.abs(v[k * N:(k + 1) * N] - r.v).max() < tol, k
+        assert U[k] == pytest.approx(r.U, rel=1e-11)
+        assert K[k] == pytest.approx(r.K, rel=1e-11)
+        assert H[k] == pytest.approx(r.H, rel=1e-11)
+
+
+def test_async_fp64_matches_oracle_at_reported_step_counts(re):
+    N, R, seed, nx = 500, 4, 31, 20
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, R)
+    ctx = re.Context(N, L, 2.5, temps, seed, precision="fp64")
+    ens = O.Ensemble(N, L, temps, seed)
+    prev = np.zeros(R, np.int64)
+    for cyc in range(3):
+        ctx.advance_async(nx)
+        steps, _ = ctx.counters()
+        made = steps - prev
+        prev = steps.copy()
+        master = cyc % R            # the attempt counter rotates the master
+        assert made[master] == nx
+        assert (made >= 1).all() and (made <= 16 * nx + 16).all(), made
+        ens.advance([int(s) for s in made])
+        compare(ctx, ens, N, L)
+        pg, ag = ctx.exchange(outputs=True)
+        po, ao = ens.exchange()
+        assert np.array_equal(pg, po) and np.array_equal(ag, ao)
+        assert np.array_equal(ctx.temps(), ens.temps())
+
+
+def test_async_graph_run_counts(re):
+    N, R, nx, cycles = 256, 8, 10, 6
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, R)
+    ctx = re.Context(N, L, 2.5, temps, 5)
+    ctx.run_async(cycles, nx, graph=True)
+    steps, _ = ctx.counters()
+    # every replica steps at least once per cycle; masters exactly nx
+    assert (steps >= cycles).all()
+    for k in range(R):
+        n_master = sum(1 for c in range(cycles) if c % R == k)
+        assert steps[k] >= n_master * nx + (cycles - n_master)
+    U, K, H = ctx.energies()
+    assert np.isfinite(U).all() and np.isfinite(K).all() and np.isfinite(H).all()
+    att, _ = ctx.accept_stats()
+    assert att.sum() == sum(1 for c in range(cycles) for k in range(c & 1, R - 1, 2))
+
+
+def test_async_replicas_run_alongside_the_master(re):
+    """All replicas resident at once (64 x 864, mixed): the others make about as
+    many steps as the master, hot replicas (more list rebuilds) somewhat fewer."""
+    N, R, nx = 864, 64, 100
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.7, 2.0, R)
+    ctx = re.Context(N, L, 2.5, temps, 3, skin=0.3)
+    ctx.advance(50)
+    s0, _ = ctx.counters()
+    ctx.advance_async(nx)
+    made = ctx.counters()[0] - s0
+    assert made[0] == nx
+    assert 0.5 * nx <= made.mean() <= 1.5 * nx, made
+
+
+def test_async_needs_batched_path(re):
+    N = 256
+    ctx = re.Context(N, inputs.box_length(N), 2.5, [1.0, 1.2], 1, path="plain")
+    with pytest.raises(re.REError):
+        ctx.advance_async(5)
