@@ -121,6 +121,33 @@ int re_advance_async(re_ctx *c, int nx);
  * CUDA graph. */
 int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
 
+/* The paper's asynchronous replica exchange inside ONE persistent launch
+ * (Implementation section): replicas integrate without stopping; in every
+ * ensemble the master of attempt a (member a mod R, rotating) waits, after nx
+ * of its own steps since it took part in attempt a - 1, until every member has
+ * finished attempt a - 1, sorts the members' temperatures and publishes the
+ * pattern (adjacent pairs in temperature order, offset by parity as in
+ * re_exchange).  Every replica looks for a new pattern after each of its
+ * steps; a paired replica publishes (T, U), waits for its partner's, and both
+ * apply the Metropolis rule with the uniform of the lower replica id for
+ * attempt a; on acceptance T is swapped and velocities scale by
+ * sqrt(T_new/T_old), exactly as re_exchange does.  n_att attempts per
+ * ensemble, then the launch ends.
+ *
+ * Requires the batched path and all replicas resident on the GPU at once
+ * (RE_EINVAL otherwise).  Every device wait is bounded (about 1 s); a wait
+ * that gives up ends the launch with RE_ETIMEOUT, reported here when logging
+ * or by the next getter.  The number of steps each replica makes is decided
+ * at run time; re_counters reports them.
+ *
+ * log_step, log_T (n_att x n_rep, row a = this call's attempt a): the
+ * replica's step count when it took part, and its temperature afterwards;
+ * log_partner: partner member id (-1 unpaired); log_acc: 1 if accepted.  Any
+ * non-NULL log pointer makes the call synchronous; with all NULL it is
+ * asynchronous. */
+int re_run_free(re_ctx *c, int n_att, int nx, int64_t *log_step, double *log_T,
+                int32_t *log_partner, uint8_t *log_acc);
+
 /* One exchange attempt in every ensemble: temperatures sorted, sorted
  * neighbours paired from offset 0 or 1, Metropolis with the lower replica
  * id's uniform, accepted pairs swap T and rescale velocities.  Outputs (host,

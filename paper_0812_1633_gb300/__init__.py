@@ -60,6 +60,9 @@ def lib():
         L.re_run.argtypes = [vp, C.c_int, i32p, C.c_int]
         L.re_advance_async.argtypes = [vp, C.c_int]
         L.re_run_async.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.re_run_free.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_uint8)]
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
@@ -171,6 +174,25 @@ class Context:
 
     def run_async(self, cycles, nx, graph=True):
         _check(lib().re_run_async(self._h, int(cycles), int(nx), 1 if graph else 0), self._h)
+
+    def run_free(self, attempts, nx, log=False):
+        """The asynchronous scheme in one persistent launch: `attempts` exchange
+        attempts per ensemble, the rotating master issuing each after nx of its
+        own steps.  With log=True returns per attempt and replica the step
+        count, temperature afterwards, partner (-1 none) and acceptance."""
+        if not log:
+            _check(lib().re_run_free(self._h, int(attempts), int(nx), None, None, None, None),
+                   self._h)
+            return None
+        shape = (int(attempts), self.n_rep)
+        st = np.zeros(shape, np.int64)
+        T = np.zeros(shape, np.float64)
+        pa = np.zeros(shape, np.int32)
+        ac = np.zeros(shape, np.uint8)
+        _check(lib().re_run_free(self._h, int(attempts), int(nx), _p(st, C.c_int64),
+                                 _p(T, C.c_double), _p(pa, C.c_int32), _p(ac, C.c_uint8)),
+               self._h)
+        return st, T, pa, ac
 
     def exchange(self, outputs=False):
         if not outputs:

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -113,6 +114,16 @@ struct re_ctx {
   bool tuning = false;              // autotune trials: no re-sorting
   std::vector<void*> allocs;
   std::string err;
+  // free-running exchange: coordination words (2 E + 5 n_rep ints), published
+  // (T, U) pairs, and the event log (grown on demand)
+  int32_t* d_fr_words = nullptr;
+  double* d_fr_slot = nullptr;
+  int64_t* d_log_step = nullptr;
+  double* d_log_T = nullptr;
+  int32_t* d_log_partner = nullptr;
+  int32_t* d_log_acc = nullptr;
+  int log_rows = 0;
+  int resident_clusters = -1;  // batched clusters resident at once (-1: not yet queried)
   // cached graph of re_run
   cudaGraphExec_t graph = nullptr;
   int graph_cycles = 0;
@@ -154,6 +165,15 @@ int dalloc(re_ctx* c, T** p, size_t n) {
   c->allocs.push_back(q);
   *p = static_cast<T*>(q);
   return RE_OK;
+}
+
+template <class T>
+void dfree(re_ctx* c, T*& p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), static_cast<void*>(p));
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+  p = nullptr;
 }
 
 int threads_for(int max_n, int cluster, int atom_threads) {
@@ -305,7 +325,7 @@ int check_cfg(re_ctx* c, const LaunchCfg& k) {
 }
 
 int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
-                   int max_budget = -1, int async_nx = 0) {
+                   int max_budget = -1, int async_nx = 0, const re::FreeDev* fr = nullptr) {
   if (c->opt.path == RE_PATH_BATCHED) {
     // renumber atoms in space order every sort_every steps (mixed path): warps
     // then hold neighbouring atoms, whose lists and gathers overlap
@@ -320,10 +340,12 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
       cudaError_t e = cudaMemsetAsync(c->s.stop, 0, sizeof(int32_t) * c->ens.size(), c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "clear stop flags");
     }
+    // the free-running modes read the lists from global memory
+    const bool budgets = async_nx <= 0 && !(fr && fr->nx > 0);
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
                                        c->opt.precision == RE_PREC_FP64, c->cfg, c->max_n,
-                                       c->max_ncell, list_elems_for(c, c->cfg), async_nx,
-                                       c->stream);
+                                       c->max_ncell, budgets ? list_elems_for(c, c->cfg) : 0,
+                                       async_nx, c->stream, fr);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
     return RE_OK;
   }
@@ -364,6 +386,10 @@ int status_check(re_ctx* c) {
     if (st[r] & (re::kStNumeric | re::kStRngCap))
       return fail(c, RE_ENUMERIC, "replica %d: non-finite energy or thermostat draw", r);
   }
+  // a timed-out wait is reported after the errors that may have caused it
+  for (int r = 0; r < c->n_rep; ++r)
+    if (st[r] & re::kStTimeout)
+      return fail(c, RE_ETIMEOUT, "replica %d: free-running exchange wait gave up", r);
   return RE_OK;
 }
 
@@ -623,6 +649,84 @@ int re_advance_async(re_ctx* c, int nx) {
     return fail(c, RE_EINVAL, "free-running mode needs the batched path");
   // the cap of the non-master replicas bounds the host's step bookkeeping
   return launch_advance(c, c->d_budget_nx, nullptr, nx, nx);
+}
+
+int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
+                int32_t* log_partner, uint8_t* log_acc) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (n_att < 0 || nx < 1) return fail(c, RE_EINVAL, "n_att >= 0 and nx >= 1 required");
+  if (c->opt.path != RE_PATH_BATCHED)
+    return fail(c, RE_EINVAL, "free-running mode needs the batched path");
+  if (n_att == 0) return RE_OK;
+  if ((int64_t)(n_att + 1) * (16 * (int64_t)nx + 16) > INT32_MAX)
+    return fail(c, RE_EINVAL, "n_att * nx too large for one launch");
+  // every replica waits for others inside the launch: all clusters must be
+  // resident at once
+  if (c->resident_clusters < 0)
+    c->resident_clusters = re::batched_max_active_clusters(c->opt.precision == RE_PREC_FP64,
+                                                           c->cfg, c->max_n, c->max_ncell);
+  if (c->n_rep > c->resident_clusters)
+    return fail(c, RE_EINVAL,
+                "free-running exchange needs all %d replicas resident at once; %d clusters of "
+                "this launch shape fit on the GPU", c->n_rep, c->resident_clusters);
+  const int E = (int)c->ens.size(), R = c->n_rep;
+  const bool want_log = log_step || log_T || log_partner || log_acc;
+  if (!c->d_fr_words) {
+    int rc;
+    if ((rc = dalloc(c, &c->d_fr_words, (size_t)2 * E + 5 * (size_t)R)) ||
+        (rc = dalloc(c, &c->d_fr_slot, 2 * (size_t)R)))
+      return rc;
+  }
+  if (want_log && c->log_rows < n_att) {
+    dfree(c, c->d_log_step);
+    dfree(c, c->d_log_T);
+    dfree(c, c->d_log_partner);
+    dfree(c, c->d_log_acc);
+    int rc;
+    const size_t n = (size_t)n_att * R;
+    if ((rc = dalloc(c, &c->d_log_step, n)) || (rc = dalloc(c, &c->d_log_T, n)) ||
+        (rc = dalloc(c, &c->d_log_partner, n)) || (rc = dalloc(c, &c->d_log_acc, n)))
+      return rc;
+    c->log_rows = n_att;
+  }
+  re::FreeDev fr{};
+  fr.nx = nx;
+  fr.n_att = n_att;
+  fr.log_cap = want_log ? n_att : 0;
+  fr.rtot = R;
+  fr.issue = c->d_fr_words;
+  fr.abort_ = fr.issue + E;
+  fr.partner = fr.abort_ + E;
+  fr.pos = fr.partner + R;
+  fr.done = fr.pos + R;
+  fr.flag = fr.done + R;
+  fr.order = fr.flag + R;
+  fr.slot = c->d_fr_slot;
+  fr.log_step = c->d_log_step;
+  fr.log_T = c->d_log_T;
+  fr.log_partner = c->d_log_partner;
+  fr.log_acc = c->d_log_acc;
+  RE_CUDA(c, cudaMemsetAsync(c->d_fr_words, 0, sizeof(int32_t) * (2 * (size_t)E + 5 * (size_t)R),
+                             c->stream), "clear exchange words");
+  int rc = launch_advance(c, c->d_budget_nx, nullptr, n_att * nx, 0, &fr);
+  if (rc) return rc;
+  RE_CUDA(c, re::launch_attempt_add(c->s, E, n_att, c->stream), "attempt counters");
+  if (!want_log) return RE_OK;
+  rc = status_check(c);
+  if (rc) return rc;
+  const size_t n = (size_t)n_att * R;
+  if (log_step)
+    RE_CUDA(c, cudaMemcpy(log_step, c->d_log_step, 8 * n, cudaMemcpyDeviceToHost), "read log");
+  if (log_T) RE_CUDA(c, cudaMemcpy(log_T, c->d_log_T, 8 * n, cudaMemcpyDeviceToHost), "read log");
+  if (log_partner)
+    RE_CUDA(c, cudaMemcpy(log_partner, c->d_log_partner, 4 * n, cudaMemcpyDeviceToHost),
+            "read log");
+  if (log_acc) {
+    std::vector<int32_t> a(n);
+    RE_CUDA(c, cudaMemcpy(a.data(), c->d_log_acc, 4 * n, cudaMemcpyDeviceToHost), "read log");
+    for (size_t k = 0; k < n; ++k) log_acc[k] = (uint8_t)a[k];
+  }
+  return RE_OK;
 }
 
 int re_run_async(re_ctx* c, int n_cycles, int nx, int use_graph) {
@@ -990,6 +1094,7 @@ int re_autotune(re_ctx* c, int steps) {
     }
   }
   c->cfg = best;
+  c->resident_clusters = -1;
   apply_cells(c, best_m);
   (void)keep_m;
   upload_tables(c);

@@ -20,7 +20,14 @@
 
 namespace re {
 
-enum StatusBits : int { kStOverflow = 1, kStNumeric = 2, kStRngCap = 4, kStStop = 8 /* not an error */ };
+enum StatusBits : int {
+  kStOverflow = 1,
+  kStNumeric = 2,
+  kStRngCap = 4,
+  kStStop = 8,     // not an error: free-running stop request seen
+  kStTimeout = 16, // free-running exchange: a bounded wait ran out, or the launch ended early
+  kStXchg = 32     // not an error: an exchange pattern is waiting at this step boundary
+};
 
 struct EnsDev {
   int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
@@ -57,6 +64,35 @@ struct StateDev {
   uint64_t* sbuf;                    // 7 words per atom: re-sort staging (scratch)
 };
 
+// Free-running replica exchange inside one persistent launch (Implementation
+// section).  Per ensemble e: `issue` counts the exchange patterns issued in
+// this launch, `abort_` is raised by a replica that leaves early.  Per replica
+// r (global index): the current pattern's partner (ensemble member id, -1 for
+// none) and position in the sorted-temperature order, the number of patterns
+// it has processed (`done`), and its published (T, U) with the pattern number
+// + 1 they belong to (`flag`).  The log holds, per pattern k < log_cap and
+// replica, the step count at which the replica took part, its temperature
+// afterwards, its partner and the decision.  Zeroed by the host before every
+// launch (except the log).
+struct FreeDev {
+  int nx;            // > 0: free-running mode; the master's own steps between patterns
+  int n_att;         // patterns per ensemble in this launch
+  int log_cap;       // patterns logged (0: none)
+  int rtot;          // replicas in the launch (log row stride)
+  int32_t* issue;    // [E]
+  int32_t* abort_;   // [E]
+  int32_t* partner;  // [Rtot]
+  int32_t* pos;      // [Rtot]
+  int32_t* done;     // [Rtot]
+  int32_t* flag;     // [Rtot]
+  int32_t* order;    // [Rtot] scratch of the master (sorted order, at the ensemble's rep_off)
+  double* slot;      // [2 Rtot] published (T, U)
+  int64_t* log_step;    // [log_cap x rtot]
+  double* log_T;        // [log_cap x rtot]
+  int32_t* log_partner; // [log_cap x rtot]
+  int32_t* log_acc;     // [log_cap x rtot]
+};
+
 struct LaunchCfg {
   int cluster, threads, cell_div, atom_threads;  // CTAs per replica, threads per CTA,
                                                  // list cells per list radius, threads per atom
@@ -72,13 +108,21 @@ cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const Re
 size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size_t list_elems);
 // list_elems > 0: each CTA keeps its atoms' neighbour sub-lists (list_elems
 // uint16 entries) in shared memory during the launch
-// async_nx > 0: free-running mode (budgets ignored): in every ensemble the
+// async_nx > 0: master-stop mode (budgets ignored): in every ensemble the
 // master replica (attempt mod R) does async_nx steps and then raises the
 // ensemble's stop flag; the others stop after the step in which they see it.
+// fr && fr->nx > 0: free-running mode with exchanges inside the launch (all
+// replicas must be resident at once; see FreeDev).  Both modes need
+// list_elems == 0 (lists in global memory).
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
                            const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
-                           int async_nx, cudaStream_t st);
+                           int async_nx, cudaStream_t st, const FreeDev* fr = nullptr);
+// Clusters of the batched kernel that can be resident at once with this
+// launch shape (0 when the query fails).
+int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int max_ncell);
+// attempt[e] += n for every ensemble (after a free-running launch)
+cudaError_t launch_attempt_add(const StateDev& s, int n_ens, int n, cudaStream_t st);
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,
                                  const EnsDev* d_ens, const RepDev* d_rep, int steps,
                                  int max_ncell, cudaStream_t st, int refresh);

@@ -32,7 +32,7 @@ constexpr int kMaxCluster = 8;
 constexpr int kMaxWarps = 32;
 constexpr int kPlainRed = 1024;  // per-replica reduction slots of the plain path
 constexpr int kNoiseChunk = 64;  // thermostat records prepared at a time (double buffered)
-constexpr int kSvrStepBytes = 40;  // sizeof(SvrStep)
+constexpr int kSvrStepBytes = 32;  // sizeof(SvrStep)
 
 // ------------------------------------------------------------------ set-up
 // FCC lattice (N = 4 k^3, cell a = L/k, four-atom basis, offset a/4) and
@@ -246,6 +246,17 @@ struct StepConst {
   int nf;
 };
 
+// The constants that depend on the thermostat's target temperature T (they
+// change when an exchange is accepted inside a free-running launch).
+__device__ __forceinline__ void set_thermo_target(StepConst& k, const EnsDev& E, double T) {
+  k.kbar = 0.5 * k.nf * T;
+  const double omc = E.tau > 0.0 ? -expm1(-E.dt / E.tau) : 0.0;  // 1 - c without cancellation
+  k.cm1f = (float)(-omc);
+  k.af = (float)(omc * k.kbar / k.nf);
+  k.bf = (float)(2.0 * sqrt(k.c_th * omc * k.kbar / k.nf));
+  k.gf = omc > 0.0 ? (float)sqrt(k.c_th * k.nf / (omc * k.kbar)) : 0.0f;
+}
+
 __device__ __forceinline__ StepConst step_const(const EnsDev& E, double T) {
   StepConst k;
   k.lam32 = E.L * 0x1.0p-32;
@@ -265,12 +276,7 @@ __device__ __forceinline__ StepConst step_const(const EnsDev& E, double T) {
   k.inv_lam2 = (float)(1.0 / (k.lam32 * k.lam32));
   k.nf = 3 * E.N - 3;
   k.c_th = E.tau > 0.0 ? exp(-E.dt / E.tau) : 1.0;
-  k.kbar = 0.5 * k.nf * T;
-  const double omc = E.tau > 0.0 ? -expm1(-E.dt / E.tau) : 0.0;  // 1 - c without cancellation
-  k.cm1f = (float)(-omc);
-  k.af = (float)(omc * k.kbar / k.nf);
-  k.bf = (float)(2.0 * sqrt(k.c_th * omc * k.kbar / k.nf));
-  k.gf = omc > 0.0 ? (float)sqrt(k.c_th * k.nf / (omc * k.kbar)) : 0.0f;
+  set_thermo_target(k, E, T);
   return k;
 }
 
@@ -529,49 +535,51 @@ __device__ __forceinline__ int group_sum(int v) {
   return v;
 }
 
-// Per-step thermostat constants, computed ahead of the step (off the critical
+// Per-step thermostat draws, generated ahead of the step (off the critical
 // path).  With K the kinetic energy after the second half kick, the SVR update
 // is K'/K = 1 + delta with delta = (c - 1) + (a + b sqrt(K)) / K, where
 // a = (1 - c) Kbar (R1^2 + S) / Nf and b = 2 R1 sqrt(c (1 - c) Kbar / Nf); the
 // factor alpha = +-sqrt(1 + delta) is negative when R1 + g sqrt(K) < 0,
 // g = sqrt(c Nf / ((1 - c) Kbar)).
 struct SvrStep {
-  double r1, s;        // the draws (FP64 path)
-  float cm1, a, b, g;  // the constants above (mixed path)
-  float r1f;           // R1 (mixed path)
-  int bad;             // the Gamma sampler hit its trial cap
+  double r1, s;  // the draws (FP64 path)
+  float r1f, sf; // the draws (mixed path)
+  int bad;       // the Gamma sampler hit its trial cap
+  int pad;
 };
 static_assert(sizeof(SvrStep) == kSvrStepBytes, "thermostat record size");
 
 __device__ inline SvrStep svr_step(bool fp64, const StepConst& K, uint64_t seed, uint64_t stream,
                                    uint64_t n, int* capped) {
   SvrStep t;
-  t.cm1 = K.cm1f;
-  t.g = K.gf;
   t.bad = 0;
+  t.pad = 0;
   if (fp64) {
     const double2 z = svr_noise(K.nf, seed, stream, n, capped);
     t.r1 = z.x;
     t.s = z.y;
-    t.a = t.b = 0.0f;
     t.r1f = (float)z.x;
+    t.sf = (float)z.y;
   } else {
     const float2 z = svr_noise_f32(K.nf, seed, stream, n, capped);
     t.r1 = z.x;
     t.s = z.y;
-    t.a = K.af * fmaf(z.x, z.x, z.y);
-    t.b = K.bf * z.x;
     t.r1f = z.x;
+    t.sf = z.y;
   }
   return t;
 }
 
 // alpha - 1 in FP32 without cancellation: sqrt(1 + delta) - 1 = delta / (1 + sqrt(1 + delta)).
-__device__ __forceinline__ float svr_eps(const SvrStep& t, float Kf) {
+// The temperature-dependent constants are read from K at the step (the
+// target may change within a launch).
+__device__ __forceinline__ float svr_eps(const SvrStep& t, float Kf, const StepConst& K) {
+  const float a = K.af * fmaf(t.r1f, t.r1f, t.sf);
+  const float b = K.bf * t.r1f;
   const float sk = sqrtf(Kf);
-  const float delta = t.cm1 + (t.a + t.b * sk) / Kf;
+  const float delta = K.cm1f + (a + b * sk) / Kf;
   const float root = sqrtf(1.0f + delta);
-  if (t.r1f + t.g * sk < 0.0f) return -1.0f - root;  // alpha = -sqrt(1 + delta)
+  if (t.r1f + K.gf * sk < 0.0f) return -1.0f - root;  // alpha = -sqrt(1 + delta)
   return delta / (1.0f + root);
 }
 
@@ -586,6 +594,131 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Metropolis rule of the Implementation section for the pair (a colder, b
+// hotter): D = (1/T_a - 1/T_b)(U_a - U_b); accept iff D >= 0 or r < exp(D),
+// r the uniform of the lower replica id for this attempt.
+__device__ __forceinline__ bool metropolis(double Ta, double Tb, double Ua, double Ub,
+                                           uint64_t seed, int id_lo, int64_t attempt) {
+  const double d = __dmul_rn(__dsub_rn(__ddiv_rn(1.0, Ta), __ddiv_rn(1.0, Tb)), __dsub_rn(Ua, Ub));
+  if (d >= 0.0) return true;
+  const Uni4 u = uniforms(seed, (uint64_t)id_lo, (uint64_t)attempt, kTagExch, 0ull);
+  return u.u0 < exp(d);
+}
+
+__device__ __forceinline__ int pair_offset(int mode, uint64_t seed, int64_t attempt) {
+  if (mode == 0) return (int)(attempt & 1);
+  const Uni4 u = uniforms(seed, ~0ull, (uint64_t)attempt, kTagParity, 0ull);
+  return u.u0 < 0.5 ? 0 : 1;
+}
+
+// ------------------------------------------------------ free-running exchange
+// The asynchronous scheme of the Implementation section inside one persistent
+// launch: every replica integrates without stopping; the master of pattern k
+// (member (attempt + k) mod R, so the role rotates with every attempt), after
+// nx of its own steps since it took part in pattern k - 1, waits until every
+// member has taken part in pattern k - 1, sorts the members' temperatures and
+// publishes pattern k.  Each replica checks for a new pattern after every
+// step; when one is there it publishes (T, U), waits for its partner's pair,
+// and both take the same Metropolis decision with the lower id's uniform.
+// Every wait is bounded (kWaitNs, and an iteration cap) and watches the
+// ensemble's abort flag; a replica that gives up or fails raises that flag.
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+__device__ bool wait_at_least(const int* p, int want, const int* abort_flag) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    if (ld_acquire(p) >= want) return true;
+    if (*reinterpret_cast<const volatile int*>(abort_flag)) return false;
+    if ((it & 63u) == 63u && global_ns() - t0 > kWaitNs) return false;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// The master's part, by one warp: pattern k of ensemble e.  Returns false when
+// a wait gave up.
+__device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsDev& E, int e, int k,
+                              int64_t attempt) {
+  const int lane = threadIdx.x & 31;
+  const int R = E.R, base = E.rep_off;
+  bool ok = true;
+  if (k > 0)
+    for (int m = lane; m < R && ok; m += 32) ok = wait_at_least(fr.done + base + m, k, fr.abort_ + e);
+  ok = __all_sync(0xffffffffu, ok);
+  if (!ok) return false;
+  __threadfence();
+  // ranks of the temperatures (positive: their bit patterns order like the values)
+  const long long* key = reinterpret_cast<const long long*>(S.T + base);
+  for (int m = lane; m < R; m += 32) {
+    const long long t = __ldcg(key + m);
+    int rank = 0;
+    for (int b = 0; b < R; ++b) {
+      const long long u = __ldcg(key + b);
+      rank += (u < t) || (u == t && b < m);
+    }
+    fr.order[base + rank] = m;
+    fr.pos[base + m] = rank;
+  }
+  __syncwarp();
+  // pairs (q, q + 1) of the sorted order for q = p, p + 2, ...
+  const int p = pair_offset(E.parity_mode, E.seed, attempt);
+  for (int m = lane; m < R; m += 32) {
+    const int q = fr.pos[base + m];
+    int partner = -1;
+    if (q >= p) {
+      if (((q - p) & 1) == 0) {
+        if (q + 1 < R) partner = fr.order[base + q + 1];
+      } else {
+        partner = fr.order[base + q - 1];
+      }
+    }
+    fr.partner[base + m] = partner;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();
+    st_release(fr.issue + e, k + 1);
+  }
+  return true;
+}
+
+// A replica's part of pattern k (one thread).  Returns the velocity scale
+// sqrt(T_new / T_old) (1 when not accepted); *ok = false when the wait gave up.
+__device__ double pair_exchange(const FreeDev& fr, const StateDev& S, const EnsDev& E,
+                                const RepDev& rd, int r, int k, int64_t attempt, double Tcur,
+                                double U, double* Tnew, int* partner_out, int* acc_out, bool* ok) {
+  const int p = __ldcg(fr.partner + r);
+  *Tnew = Tcur;
+  *partner_out = p;
+  *acc_out = 0;
+  *ok = true;
+  if (p < 0) return 1.0;
+  fr.slot[2 * r] = Tcur;
+  fr.slot[2 * r + 1] = U;
+  __threadfence();
+  st_release(fr.flag + r, k + 1);
+  const int gp = E.rep_off + p;
+  if (!wait_at_least(fr.flag + gp, k + 1, fr.abort_ + rd.ens)) {
+    *ok = false;
+    return 1.0;
+  }
+  __threadfence();
+  const double Tp = __ldcg(fr.slot + 2 * gp), Up = __ldcg(fr.slot + 2 * gp + 1);
+  const int q = __ldcg(fr.pos + r), qp = __ldcg(fr.pos + gp);
+  const bool colder = q < qp;
+  const int id_lo = min(rd.id, p);
+  const bool accept = colder ? metropolis(Tcur, Tp, U, Up, E.seed, id_lo, attempt)
+                             : metropolis(Tp, Tcur, Up, U, E.seed, id_lo, attempt);
+  if (colder) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(S.pair_att + E.pair_off + q), 1ull);
+    if (accept) atomicAdd(reinterpret_cast<unsigned long long*>(S.pair_acc + E.pair_off + q), 1ull);
+  }
+  if (!accept) return 1.0;
+  *acc_out = 1;
+  *Tnew = Tp;
+  return sqrt(Tp / Tcur);
 }
 
 // One thread-block cluster per replica (work item).  CTA `crank` owns atoms
@@ -604,13 +737,15 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
 // integers (exact, order independent).  The second half kick, the thermostat
 // factor and the next first half kick form one increment per coordinate.
 // FP64 path: FP64 state arithmetic and FP64 pair forces throughout.
-template <bool FP64, int P, bool LSM>
+// MODE 0: per-replica step budgets; 1: master-stop (dims.async_nx); 2:
+// free-running with exchanges inside the launch (fr).
+template <bool FP64, int P, bool LSM, int MODE>
 __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
                                                              const EnsDev* __restrict__ ens,
                                                              const RepDev* __restrict__ reps,
                                                              const int* __restrict__ work,
                                                              const int32_t* __restrict__ budget,
-                                                             KernelDims dims) {
+                                                             KernelDims dims, FreeDev fr) {
   constexpr int ND = (3 + P - 1) / P;  // coordinates per lane
   // replica constants live in shared memory, not in registers
   __shared__ EnsDev E;
@@ -618,6 +753,12 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   __shared__ double alpha_sh, kp_sh;
   __shared__ float eps_sh;
   __shared__ int st_sh;
+  // free-running exchange: the result handed to the cluster (velocity scale,
+  // new T, status), the replica's current T and the launch's first attempt
+  // number (thread 0), own steps since the last pattern (warp 0 of CTA 0)
+  __shared__ double xs_sh, xT_sh, Tcur_sh;
+  __shared__ long long A0_sh;
+  __shared__ int xst_sh, since_sh, fold0_sh;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
@@ -626,6 +767,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   if (threadIdx.x == 0) {
     E = ens[rd.ens];
     K = step_const(E, S.T[r]);
+    Tcur_sh = S.T[r];
+    A0_sh = S.attempt[rd.ens];
+    since_sh = 0;
+    fold0_sh = 0;
   }
   const int T = blockDim.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nw = (T + 31) >> 5;
@@ -635,10 +780,13 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // does async_nx steps and then raises the ensemble's stop flag; every other
   // replica checks the flag after each step and stops after the step in which
   // it sees it (at most kAsyncCapFactor * async_nx + 16 steps).  No thread waits.
-  const int async_nx = dims.async_nx;
+  const int async_nx = MODE == 1 ? dims.async_nx : 0;
+  constexpr bool freerun = MODE == 2;
   bool is_master = false;
   int B;
-  if (async_nx > 0) {
+  if (freerun) {
+    B = (fr.n_att + 1) * (kAsyncCapFactor * fr.nx + 16);  // step cap of the launch
+  } else if (async_nx > 0) {
     const int Rens = ens[rd.ens].R;
     is_master = rd.id == (int)(S.attempt[rd.ens] % Rens);
     B = is_master ? async_nx : kAsyncCapFactor * async_nx + 16;
@@ -660,7 +808,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // Every CTA has read the replica's flags before any CTA may change them
   // (the barrier also publishes E and K to the whole CTA).
   cl.sync();
-  if (status0 != 0 || (B <= 0 && valid0)) return;  // uniform over the cluster
+  if (status0 != 0 || (B <= 0 && valid0)) {  // uniform over the cluster
+    // a replica that cannot run must not leave its partners waiting
+    if (freerun && crank == 0 && threadIdx.x == 0) atomicExch(fr.abort_ + rd.ens, 1);
+    return;
+  }
   // a one-CTA replica synchronises with the cheaper block barrier
   auto csync = [&]() {
     if (C > 1)
@@ -936,8 +1088,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     }
   }
 
+  int k_next = 0;           // free-running: next pattern to take part in (uniform)
+  bool first_kick = true;  // the step starts with a first half kick
+
   int done = 0;
-  for (int s = 0; s < B && status == 0; ++s) {
+  for (int s = 0; s < B && status == 0 && !(freerun && k_next >= fr.n_att); ++s) {
     const int64_t n = step0 + s;
     SvrStep* sv = reinterpret_cast<SvrStep*>(sm.noise) + ((s / kNoiseChunk) & 1) * kNoiseChunk;
     if (thermo && (s % kNoiseChunk) == 0 && tid < kNoiseChunk && s + tid < B) {
@@ -954,10 +1109,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         const int d = q + j * P;
         if (d >= 3) continue;
         if (FP64) {
-          if (s == 0) v[j] += K.hdt * f[j];
+          if (first_kick) v[j] += K.hdt * f[j];
           xq[j] += (uint64_t)__double2ll_rn(v[j] * K.dtq);
         } else {
-          if (s == 0) {
+          if (first_kick) {
             vq[j] += f2ll_split(hf[j] * kVelScale);
             vf[j] = ll2f_split(vq[j]) * kVelUnit;
           }
@@ -981,22 +1136,43 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     if (mdall > K.half2u) rebuild();
     // the pair energies are summed only when U is reported (the last step;
     // every step in free-running mode, where the last step is not known ahead)
-    forces_and_publish(true, async_nx > 0 || s + 1 == B, overflow);
-    // free-running mode: CTA 0 reads the master's flag and tells every CTA of
+    forces_and_publish(true, async_nx > 0 || freerun || s + 1 == B, overflow);
+    // master-stop mode: CTA 0 reads the master's flag and tells every CTA of
     // the cluster (through the status slots) that this step is the last
     if (async_nx > 0 && !is_master && crank == 0 && tid == 0) {
       if (*reinterpret_cast<volatile int32_t*>(S.stop + rd.ens))
         for (int rk = 0; rk < C; ++rk) atomicOr(cl.map_shared_rank(sm.slot_st, rk), (int)kStStop);
     }
+    if (freerun) {
+      // the master of the next pattern issues it after nx of its own steps
+      if (crank == 0 && warp == 0 && k_next < fr.n_att && since_sh + 1 >= fr.nx &&
+          rd.id == (int)((A0_sh + k_next) % E.R)) {
+        if (!issue_pattern(fr, S, E, rd.ens, k_next, A0_sh + k_next) && lane == 0)
+          atomicExch(fr.abort_ + rd.ens, 1);
+      }
+      // CTA 0 looks for a new pattern (or an abort) and tells every CTA
+      if (crank == 0 && tid == 0) {
+        int bits = 0;
+        if (ld_acquire(fr.issue + rd.ens) > k_next) bits |= kStXchg;
+        if (*reinterpret_cast<volatile int32_t*>(fr.abort_ + rd.ens)) bits |= kStStop;
+        if (bits)
+          for (int rk = 0; rk < C; ++rk) atomicOr(cl.map_shared_rank(sm.slot_st, rk), bits);
+      }
+    }
     csync();  // B2
     int st;
-    const SvrStep z = thermo ? sv[s % kNoiseChunk] : SvrStep{0.0, 0.0, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-    // the stop bit is in every CTA's slots after B2: read it before the update
+    const SvrStep z = thermo ? sv[s % kNoiseChunk] : SvrStep{0.0, 0.0, 0.f, 0.f, 0, 0};
+    // the stop and exchange bits are in every CTA's slots after B2: read them
+    // before the update
     const bool stop_seen = (sm.slot_st[0] & kStStop) != 0;
+    const bool xchg = freerun && (sm.slot_st[0] & kStXchg) != 0;
     const bool last = (s + 1 == B) || stop_seen;
+    // the step ends on a materialised step boundary (velocities at full step)
+    const bool bnd = last || xchg;
     if (FP64) {
       double su, sk;
       totals_fp64(su, sk, st);
+      st &= ~(int)kStXchg;
       if (z.bad) st |= kStRngCap;
       const double Un = 0.5 * su, Kn = 0.5 * sk;
       // one lane forms the FP64 factor and K'; the CTA reads both after the
@@ -1015,7 +1191,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
 #pragma unroll
         for (int j = 0; j < ND; ++j) {
           v[j] *= alpha;
-          if (!last) v[j] += K.hdt * f[j];  // first half kick of the next step
+          if (!bnd) v[j] += K.hdt * f[j];  // first half kick of the next step
         }
       }
       U = Un;
@@ -1027,9 +1203,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       long long iu = 0, ik = 0;
       if (warp == 0) {
         totals_int(iu, ik, st);
+        st &= ~(int)kStXchg;
         if (z.bad) st |= kStRngCap;
         const float Kf = ll2f_split(ik) * (float)(0.5 * kEnUnit);
-        const float e0 = thermo ? svr_eps(z, Kf) : 0.0f;
+        const float e0 = thermo ? svr_eps(z, Kf, K) : 0.0f;
         if (!isfinite(e0)) st |= kStNumeric;
         if (lane == 0) {
           eps_sh = e0;
@@ -1046,7 +1223,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           if (d >= 3) continue;
           const float w = vf[j] + hf[j];
           // second half kick + thermostat factor (+ next first half kick)
-          const float inc = fmaf(eps, w, last ? hf[j] : 2.0f * hf[j]);
+          const float inc = fmaf(eps, w, bnd ? hf[j] : 2.0f * hf[j]);
           vq[j] += f2ll_split(inc * kVelScale);
           vf[j] = ll2f_split(vq[j]) * kVelUnit;
         }
@@ -1060,19 +1237,22 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           sm.rec_k[slot] = ik;
           sm.rec_e[slot] = eps;
         }
-        if (slot == kNoiseChunk - 1 || last) {
+        if (slot == kNoiseChunk - 1 || bnd) {
           __syncwarp();
           double dsum = 0.0, kp = 0.0;
-          for (int t = lane; t <= slot; t += 32) {
+          const int fold0 = fold0_sh;
+          for (int t = fold0 + lane; t <= slot; t += 32) {
             const double Kn = 0.5 * (double)sm.rec_k[t] * kEnUnit;
             const double a1 = 1.0 + (double)sm.rec_e[t];
             dsum += Kn - Kn * a1 * a1;
             if (t == slot) kp = Kn * a1 * a1;
           }
           econs += warp_sum(dsum);
-          kp = __shfl_sync(0xffffffffu, kp, slot & 31);
+          kp = __shfl_sync(0xffffffffu, kp, (slot - fold0) & 31);
           Kin = kp;
           U = 0.5 * (double)iu * kEnUnit;
+          __syncwarp();
+          if (lane == 0) fold0_sh = slot + 1 == kNoiseChunk ? 0 : slot + 1;
           __syncwarp();
         }
       }
@@ -1084,6 +1264,70 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       __threadfence();
       atomicExch(S.stop + rd.ens, 1);
     }
+    if (xchg) {
+      // this replica's part of the pattern: CTA 0 runs the pair protocol and
+      // hands the result to every CTA of the cluster
+      if (crank == 0 && tid == 0) {
+        double Tn;
+        int pid, acc;
+        bool ok;
+        const double sc = pair_exchange(fr, S, E, rd, r, k_next, A0_sh + k_next, Tcur_sh, U, &Tn,
+                                        &pid, &acc, &ok);
+        if (k_next < fr.log_cap) {
+          const size_t li = (size_t)k_next * fr.rtot + r;
+          fr.log_step[li] = step0 + done;
+          fr.log_T[li] = Tn;
+          fr.log_partner[li] = pid;
+          fr.log_acc[li] = acc;
+        }
+        if (Tn != Tcur_sh) S.T[r] = Tn;
+        for (int rk = 0; rk < C; ++rk) {
+          *cl.map_shared_rank(&xs_sh, rk) = sc;
+          *cl.map_shared_rank(&xT_sh, rk) = Tn;
+          *cl.map_shared_rank(&xst_sh, rk) = ok ? 0 : (int)kStTimeout;
+        }
+      }
+      csync();  // B3
+      const double sc = xs_sh, Tn = xT_sh;
+      status |= xst_sh;
+      if (tid == 0) atomicAnd(&sm.slot_st[0], ~(int)kStXchg);
+      if (own && sc != 1.0) {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          const int d = q + j * P;
+          if (d >= 3) continue;
+          if (FP64) {
+            v[j] *= sc;
+          } else {
+            vq[j] = __double2ll_rn((double)vq[j] * sc);
+            vf[j] = ll2f_split(vq[j]) * kVelUnit;
+          }
+        }
+      }
+      const double Ks = Kin * (sc * sc);
+      econs += Kin - Ks;
+      Kin = Ks;
+      if (tid == 0) {
+        if (Tn != Tcur_sh) {
+          set_thermo_target(K, E, Tn);  // read by others only after the next barriers
+          Tcur_sh = Tn;
+        }
+        since_sh = 0;
+      }
+      if (crank == 0 && tid == 0) {
+        __threadfence();
+        st_release(fr.done + r, k_next + 1);
+      }
+      ++k_next;
+    } else if (freerun && tid == 0) {
+      ++since_sh;
+    }
+    first_kick = bnd;
+  }
+  if (freerun && k_next < fr.n_att) {
+    // left before the last pattern: the partners' waits must not run out
+    if (crank == 0 && tid == 0) atomicExch(fr.abort_ + rd.ens, 1);
+    if ((status & ~(int)kStStop) == 0) status |= kStTimeout;
   }
   // shared-memory lists go back to global memory for the next launch
   if (LSM) {
@@ -1121,7 +1365,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     S.step[r] = step0 + done;
     S.nreb[r] += nreb;
     S.vscale[r] = 1.0;
-    S.status[r] = status & ~kStStop;
+    S.status[r] = status & ~(int)(kStStop | kStXchg);
     S.valid[r] = (status & kStOverflow) ? 0 : 1;
   }
   cl.sync();  // no CTA leaves while another may still touch its shared memory
@@ -1320,23 +1564,6 @@ __global__ void plain_thermo(StateDev S, const EnsDev* __restrict__ ens,
 }
 
 // ------------------------------------------------------------------ exchange
-// Metropolis rule of the Implementation section for the pair (a colder, b
-// hotter): D = (1/T_a - 1/T_b)(U_a - U_b); accept iff D >= 0 or r < exp(D),
-// r the uniform of the lower replica id for this attempt.
-__device__ __forceinline__ bool metropolis(double Ta, double Tb, double Ua, double Ub,
-                                           uint64_t seed, int id_lo, int64_t attempt) {
-  const double d = __dmul_rn(__dsub_rn(__ddiv_rn(1.0, Ta), __ddiv_rn(1.0, Tb)), __dsub_rn(Ua, Ub));
-  if (d >= 0.0) return true;
-  const Uni4 u = uniforms(seed, (uint64_t)id_lo, (uint64_t)attempt, kTagExch, 0ull);
-  return u.u0 < exp(d);
-}
-
-__device__ __forceinline__ int pair_offset(int mode, uint64_t seed, int64_t attempt) {
-  if (mode == 0) return (int)(attempt & 1);
-  const Uni4 u = uniforms(seed, ~0ull, (uint64_t)attempt, kTagParity, 0ull);
-  return u.u0 < 0.5 ? 0 : 1;
-}
-
 // Sorted order of R distinct temperatures by counting (rank = number of
 // smaller values, ties broken by index).  Ts, order in shared memory.  The
 // temperatures are positive, so their IEEE bit patterns read as 64-bit
@@ -1595,13 +1822,14 @@ size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size
   return batched_layout(max_n, max_ncell, threads, fp64, list_elems, nullptr, nullptr);
 }
 
-template <bool FP64, int P, bool LSM>
+template <bool FP64, int P, bool LSM, int MODE>
 static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                    const int* d_work, int n_work, const int32_t* d_budget,
                                    const LaunchCfg& cfg, int max_n, int max_ncell,
-                                   size_t list_elems, int async_nx, cudaStream_t st) {
+                                   size_t list_elems, int async_nx, cudaStream_t st,
+                                   const FreeDev* fr) {
   const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
-  auto fn = md_batched_kernel<FP64, P, LSM>;
+  auto fn = md_batched_kernel<FP64, P, LSM, MODE>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // the rest of the SM's 256 KB serves as L1 (lists in global memory, state)
@@ -1624,29 +1852,94 @@ static cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, cons
   lc.attrs = at;
   lc.numAttrs = 1;
   KernelDims dims{max_n, max_ncell, list_elems, async_nx};
-  return cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims);
+  FreeDev f{};
+  if (fr) f = *fr;
+  return cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims, f);
+}
+
+template <bool FP64, int P, bool LSM>
+static int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell,
+                                 size_t list_elems) {
+  const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
+  auto fn = md_batched_kernel<FP64, P, LSM, 2>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)cfg.cluster);
+  lc.blockDim = dim3((unsigned)cfg.threads);
+  lc.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cfg.cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &lc) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int max_ncell) {
+#define RE_MC(F, PP) return max_active_clusters_t<F, PP, false>(cfg, max_n, max_ncell, 0);
+#define RE_MCP(F)             \
+  switch (cfg.atom_threads) { \
+    case 1: RE_MC(F, 1)       \
+    case 2: RE_MC(F, 2)       \
+    case 4: RE_MC(F, 4)       \
+    case 8: RE_MC(F, 8)       \
+  }
+  if (fp64) {
+    RE_MCP(true)
+  } else {
+    RE_MCP(false)
+  }
+#undef RE_MCP
+#undef RE_MC
+  return 0;
+}
+
+__global__ void attempt_add_kernel(StateDev S, int n_ens, int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n_ens) S.attempt[e] += n;
+}
+
+cudaError_t launch_attempt_add(const StateDev& s, int n_ens, int n, cudaStream_t st) {
+  attempt_add_kernel<<<(n_ens + 127) / 128, 128, 0, st>>>(s, n_ens, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                            const int* d_work, int n_work, const int32_t* d_budget, bool fp64,
                            const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems,
-                           int async_nx, cudaStream_t st) {
+                           int async_nx, cudaStream_t st, const FreeDev* fr) {
   if (n_work <= 0) return cudaSuccess;
   const bool lsm = list_elems > 0;
-#define RE_LB(F, PP, LS)                                                                      \
-  return launch_batched_t<F, PP, LS>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg, max_n,  \
-                                     max_ncell, list_elems, async_nx, st);
-#define RE_LBP(F, LS)                              \
+  const int mode = (fr && fr->nx > 0) ? 2 : (async_nx > 0 ? 1 : 0);
+  // the two free-running modes keep the lists in global memory
+  if (mode != 0 && lsm) return cudaErrorInvalidValue;
+#define RE_LB(F, PP, LS, M)                                                                   \
+  return launch_batched_t<F, PP, LS, M>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg,      \
+                                        max_n, max_ncell, list_elems, async_nx, st, fr);
+#define RE_LBP(F, LS, M)                           \
   switch (cfg.atom_threads) {                      \
-    case 1: RE_LB(F, 1, LS)                        \
-    case 2: RE_LB(F, 2, LS)                        \
-    case 4: RE_LB(F, 4, LS)                        \
-    case 8: RE_LB(F, 8, LS)                        \
+    case 1: RE_LB(F, 1, LS, M)                     \
+    case 2: RE_LB(F, 2, LS, M)                     \
+    case 4: RE_LB(F, 4, LS, M)                     \
+    case 8: RE_LB(F, 8, LS, M)                     \
   }
-  if (fp64) {
-    if (lsm) { RE_LBP(true, true) } else { RE_LBP(true, false) }
+  if (mode == 1) {
+    if (fp64) { RE_LBP(true, false, 1) } else { RE_LBP(false, false, 1) }
+  } else if (mode == 2) {
+    if (fp64) { RE_LBP(true, false, 2) } else { RE_LBP(false, false, 2) }
+  } else if (fp64) {
+    if (lsm) { RE_LBP(true, true, 0) } else { RE_LBP(true, false, 0) }
   } else {
-    if (lsm) { RE_LBP(false, true) } else { RE_LBP(false, false) }
+    if (lsm) { RE_LBP(false, true, 0) } else { RE_LBP(false, false, 0) }
   }
 #undef RE_LBP
 #undef RE_LB

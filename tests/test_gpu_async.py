@@ -102,3 +102,69 @@ def test_async_needs_batched_path(re):
     ctx = re.Context(N, inputs.box_length(N), 2.5, [1.0, 1.2], 1, path="plain")
     with pytest.raises(re.REError):
         ctx.advance_async(5)
+
+
+# ---------------------------------------------------------------------------
+# exchanges inside one persistent launch (re_run_free)
+
+def test_free_running_fp64_replays_on_the_oracle(re):
+    """The log gives, per attempt, the step at which each replica took part;
+    the oracle advanced to those steps and exchanging there must take the same
+    decisions and land on the same states."""
+    N, R, seed, nx, A = 256, 8, 41, 10, 12
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, R)
+    ctx = re.Context(N, L, 2.5, temps, seed, precision="fp64")
+    ens = O.Ensemble(N, L, temps, seed)
+    steps, T, partner, acc = ctx.run_free(A, nx, log=True)
+    prev = np.zeros(R, np.int64)
+    for k in range(A):
+        m = k % R
+        # the master issues attempt k nx of its own steps after its attempt k - 1
+        assert steps[k, m] - prev[m] == nx, (k, steps[k], prev)
+        made = steps[k] - prev
+        assert (made >= 1).all(), made
+        ens.advance([int(x) for x in made])
+        po, ao = ens.exchange()
+        assert np.array_equal(partner[k], po), (k, partner[k], po)
+        assert np.array_equal(acc[k].astype(bool), ao.astype(bool)), k
+        assert np.array_equal(T[k], ens.temps()), k
+        prev = steps[k].copy()
+    assert np.array_equal(ctx.counters()[0], prev)
+    compare(ctx, ens, N, L, tol=1e-9)
+    att, _ = ctx.accept_stats()
+    assert att.sum() == sum(1 for k in range(A) for q in range(k & 1, R - 1, 2))
+
+
+def test_free_running_mixed_many_replicas(re):
+    N, R, nx, A = 864, 64, 10, 40
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.7, 2.0, R)
+    ctx = re.Context(N, L, 2.5, temps, 3, skin=0.3)
+    ctx.advance(20)
+    s0, _ = ctx.counters()
+    steps, T, partner, acc = ctx.run_free(A, nx, log=True)
+    for k in range(A):
+        assert np.array_equal(np.sort(T[k]), np.sort(temps))      # still a permutation
+        p = partner[k]
+        for r in range(R):                                          # pairs are mutual
+            if p[r] >= 0:
+                assert p[p[r]] == r and acc[k, r] == acc[k, p[r]]
+    per_attempt = (steps[-1] - s0) / A                              # <N_x> per replica
+    assert 0.5 * nx <= per_attempt.mean() <= 2.0 * nx, per_attempt
+    U, K, H = ctx.energies()
+    assert np.isfinite(U).all() and np.isfinite(K).all()
+    assert np.array_equal(ctx.temps(), T[-1])
+    # the context goes on with ordinary cycles afterwards
+    ctx.advance(10)
+    ctx.exchange()
+    ctx.run_free(5, nx)
+    assert np.isfinite(ctx.energies()[0]).all()
+
+
+def test_free_running_refuses_non_resident_launch(re):
+    N, R = 256, 1000
+    L = inputs.box_length(N)
+    ctx = re.Context(N, L, 2.5, inputs.geometric_ladder(0.7, 2.0, R), 1)
+    with pytest.raises(re.REError):
+        ctx.run_free(2, 5)
