@@ -493,6 +493,159 @@ def run_drift(args):
     print(json.dumps(out), flush=True)
 
 
+def melted_context(re, N, temps, seed, **kw):
+    """A liquid on the ladder: melted at T 2.0-2.2 from the FCC start, velocities
+    rescaled to the ladder, 200 steps on it."""
+    L = inputs.box_length(N)
+    temps = np.asarray(temps, dtype=np.float64)
+    hot = inputs.geometric_ladder(2.0, 2.2, len(temps))
+    m = re.Context(N, L, 2.5, hot, seed, **kw)
+    m.advance(2000)
+    x, v = m.get_state()
+    m.close()
+    ctx = re.Context(N, L, 2.5, temps, seed + 1, **kw)
+    ctx.set_state(x, v * np.repeat(np.sqrt(temps / hot), N)[:, None])
+    ctx.advance(200)
+    return ctx
+
+
+def timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def run_lambda(args):
+    """Parallel efficiency lambda (Example section, Scalability): total steps of
+    all replicas per wall-clock second with exchanges, divided by the same
+    without exchanges, against the number of replicas."""
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    build.build()
+    N, nx, A = args.lam_n, args.lam_nx, args.lam_attempts
+    out = {"study": "parallel efficiency lambda vs replicas",
+           "workload": f"R replicas x {N} atoms, rho 0.8442, T 0.7-2.5 geometric, skin 0.3, "
+                       f"mixed, melted start; N_x {nx}; {A} attempts per measurement",
+           "modes": {"no_exchange": "one launch, every replica runs until the master has made "
+                                    f"{A}*N_x steps (the lambda denominator)",
+                     "sync": "per attempt: one launch of N_x steps per replica, then the "
+                             "exchange kernel (CUDA graph)",
+                     "master_stop": "per attempt: one launch ended by the rotating master "
+                                    "after N_x steps, then the exchange kernel (CUDA graph)",
+                     "async": "one launch; exchanges between replicas inside it (rotating "
+                              "master, pairwise waits)"},
+           "rows": []}
+    for R in [int(v) for v in args.lam_rs.split(",")]:
+        temps = inputs.geometric_ladder(0.7, 2.5, R)
+        ctx = melted_context(re, N, temps, 777, skin=0.3, nx=nx)
+        row = {"R": R, "launch": ctx.config()}
+        cnt = lambda: ctx.counters()[0].astype(np.float64)
+        # warm-up of every mode (graphs, lazily allocated buffers)
+        ctx.advance_async(nx)
+        ctx.run(2)
+        ctx.run_async(2, nx)
+        try:
+            ctx.run_free(2, nx)
+            free_ok = True
+        except re.REError as e:
+            free_ok = False
+            row["async"] = {"unavailable": str(e)}
+        s0 = cnt()
+        t = timed(torch, lambda: ctx.advance_async(A * nx))
+        rate0 = (cnt() - s0).sum() / t
+        row["no_exchange"] = {"replica_steps_per_s": rate0}
+        t = timed(torch, lambda: ctx.run(A))
+        r_sync = R * nx * A / t
+        row["sync"] = {"replica_steps_per_s": r_sync, "lambda": r_sync / rate0, "mean_nx": nx}
+        s0 = cnt()
+        t = timed(torch, lambda: ctx.run_async(A, nx))
+        d = cnt() - s0
+        row["master_stop"] = {"replica_steps_per_s": d.sum() / t, "lambda": d.sum() / t / rate0,
+                              "mean_nx": d.sum() / (R * A)}
+        if free_ok:
+            s0 = cnt()
+            t = timed(torch, lambda: ctx.run_free(A, nx))
+            d = cnt() - s0
+            row["async"] = {"replica_steps_per_s": d.sum() / t, "lambda": d.sum() / t / rate0,
+                            "mean_nx": d.sum() / (R * A)}
+        att, acc = ctx.accept_stats()
+        row["acceptance"] = float(acc.sum() / max(att.sum(), 1))
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+        ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+def msd_diffusion(logT, steps, max_lag=10):
+    """D of ln T: half the slope of the mean squared displacement of ln T against
+    elapsed steps, over lags of 1..max_lag attempts (least squares through 0).
+    logT, steps: (attempts, replicas)."""
+    y = np.log(logT)
+    lags, msd = [], []
+    for m in range(1, max_lag + 1):
+        dy = y[m:] - y[:-m]
+        ds = steps[m:] - steps[:-m]
+        lags.append(ds.mean())
+        msd.append((dy * dy).mean())
+    lags, msd = np.asarray(lags), np.asarray(msd)
+    return float((lags * msd).sum() / (lags * lags).sum() / 2.0)
+
+
+def run_diffusion(args):
+    """Diffusion coefficient of ln T against the observed exchange stride <N_x>
+    (Example section, Diffusion in temperature space) for the synchronous and
+    the asynchronous (in-launch) schemes."""
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    build.build()
+    N, R, A = args.dif_n, args.dif_r, args.dif_attempts
+    ratio = args.dif_ratio
+    temps = 0.7 * ratio ** np.arange(R)
+    out = {"study": "diffusion coefficient of ln T vs <N_x>",
+           "workload": f"{R} replicas x {N} atoms, rho 0.8442, T_k = 0.7 * {ratio}^k, skin 0.3, "
+                       f"mixed, melted start, {A} attempts per point, cluster "
+                       f"{args.dif_cluster}",
+           "estimator": "half the least-squares slope (through 0) of <(ln T(t+s) - ln T(t))^2> "
+                        "against the elapsed steps s, lags of 1-10 attempts",
+           "rows": []}
+    for nx in [int(v) for v in args.dif_nx.split(",")]:
+        row = {"nx": nx}
+        # one launch shape for both schemes, with every replica resident
+        shape = dict(skin=0.3, nx=nx, cluster=args.dif_cluster, atom_threads=1)
+        ctx = melted_context(re, N, temps, 4242, **shape)
+        base = ctx.counters()[0]
+        Ts, st = [], []
+        for k in range(A):
+            ctx.advance(nx)
+            ctx.exchange()
+            Ts.append(ctx.temps())
+            st.append(ctx.counters()[0] - base)
+        att, acc = ctx.accept_stats()
+        row["sync"] = {"D": msd_diffusion(np.array(Ts), np.array(st)), "mean_nx": nx,
+                       "acceptance": float(acc.sum() / att.sum())}
+        ctx.close()
+        ctx = melted_context(re, N, temps, 4242, **shape)
+        try:
+            a0, c0 = ctx.accept_stats()
+            base = ctx.counters()[0]
+            steps, T, _, _ = ctx.run_free(A, nx, log=True)
+            att, acc = ctx.accept_stats()
+            steps = steps - base
+            mean_nx = float(np.diff(np.vstack([np.zeros((1, R)), steps]), axis=0).mean())
+            row["async"] = {"D": msd_diffusion(T, steps.astype(np.float64)), "mean_nx": mean_nx,
+                            "acceptance": float((acc - c0).sum() / (att - a0).sum())}
+        except re.REError as e:
+            row["async"] = {"unavailable": str(e)}
+        ctx.close()
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,8 +656,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
-    ap.add_argument("--study", default=None, choices=["drift"],
+    ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion"],
                     help="run a study instead of the throughput bench")
+    ap.add_argument("--lam-n", type=int, default=864)
+    ap.add_argument("--lam-nx", type=int, default=5)
+    ap.add_argument("--lam-attempts", type=int, default=400)
+    ap.add_argument("--lam-rs", default="8,16,32,64,96,128,152")
+    ap.add_argument("--dif-n", type=int, default=2048)
+    ap.add_argument("--dif-r", type=int, default=48)
+    ap.add_argument("--dif-ratio", type=float, default=1.0386)
+    ap.add_argument("--dif-attempts", type=int, default=2000)
+    ap.add_argument("--dif-nx", default="1,2,5,10,20")
+    ap.add_argument("--dif-cluster", type=int, default=2)
     ap.add_argument("--drift-n", type=int, default=4000)
     ap.add_argument("--drift-r", type=int, default=8)
     ap.add_argument("--drift-steps", type=int, default=20000)
@@ -517,6 +680,12 @@ def main():
     cfg = CONFIGS[args.config]
     if args.study == "drift":
         run_drift(args)
+        return
+    if args.study == "lambda":
+        run_lambda(args)
+        return
+    if args.study == "diffusion":
+        run_diffusion(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)
