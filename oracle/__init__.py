@@ -283,6 +283,21 @@ class Ensemble:
         R = len(self.reps)
         self._arr = (C.POINTER(Rep) * R)(*[C.pointer(r.rep) for r in self.reps])
 
+    @classmethod
+    def from_state(cls, N, L, temps, seed, x, v, **kw):
+        """An ensemble whose replica k starts at positions x[k], velocities v[k]
+        (arrays of shape (R, N, 3)) instead of the lattice."""
+        ens = cls.__new__(cls)
+        rc, skin = kw.get("rc", 2.5), kw.get("skin", 0.5)
+        dt, tau, shift = kw.get("dt", 0.005), kw.get("tau", 0.5), kw.get("shift", 1)
+        ens.reps = [Replica(N, L, float(T), seed, k, rc, skin, dt, tau, shift, x=x[k], v=v[k])
+                    for k, T in enumerate(temps)]
+        ens.seed = seed
+        ens.attempt = 0
+        ens.parity_mode = kw.get("parity_mode", 0)
+        ens._arr = (C.POINTER(Rep) * len(ens.reps))(*[C.pointer(r.rep) for r in ens.reps])
+        return ens
+
     @property
     def R(self):
         return len(self.reps)

@@ -17,6 +17,7 @@
 #include "re_internal.h"
 
 using re::EnsDev;
+using re::finish_ens;
 using re::LaunchCfg;
 using re::RepDev;
 using re::StateDev;
@@ -166,6 +167,44 @@ int dalloc(re_ctx* c, T** p, size_t n) {
   *p = static_cast<T*>(q);
   return RE_OK;
 }
+
+}  // namespace
+
+namespace re {
+void finish_ens(EnsDev& e) {
+  StepConst& k = e.kc;
+  k = StepConst{};
+  k.lam32 = e.L * 0x1.0p-32;
+  k.lam64 = e.L * 0x1.0p-64;
+  k.inv_l = 1.0 / e.L;
+  k.dtq = e.dt * 0x1.0p64 / e.L;
+  k.hdt = 0.5 * e.dt;
+  k.inv_hdt = 1.0 / k.hdt;
+  const double rc6 = e.rc * e.rc * e.rc * e.rc * e.rc * e.rc;
+  k.uc = e.shift ? 4.0 * (1.0 / (rc6 * rc6) - 1.0 / rc6) : 0.0;
+  k.rc2 = e.rc * e.rc;
+  const double rcu = e.rc / k.lam32;
+  k.rc2u = (float)(rcu * rcu);
+  // list radius rounded up, half skin rounded down: the list never misses a pair
+  const double rlu = e.rlist * (1.0 + 1e-6) / k.lam32;
+  k.rl2u = (float)(rlu * rlu);
+  const double hu = 0.5 * e.skin * (1.0 - 1e-6) / k.lam32;
+  k.half2u = (float)(hu * hu);
+  k.inv_lam2 = (float)(1.0 / (k.lam32 * k.lam32));
+  k.nf = 3 * e.N - 3;
+  k.c_th = e.tau > 0.0 ? std::exp(-e.dt / e.tau) : 1.0;
+  const double omc = e.tau > 0.0 ? -std::expm1(-e.dt / e.tau) : 0.0;  // 1 - c, no cancellation
+  k.cm1f = (float)(-omc);
+  // Kbar = Nf T / 2: a = (1 - c) T / 2, b = 2 sqrt(c (1 - c) T / 2), g = sqrt(2 c / ((1 - c) T))
+  k.kbar1 = 0.5 * k.nf;
+  k.af1 = 0.5 * omc;
+  k.bf1 = 2.0 * std::sqrt(0.5 * k.c_th * omc);
+  k.gf1 = omc > 0.0 ? std::sqrt(2.0 * k.c_th / omc) : 0.0;
+  set_thermo_target(k, 1.0);
+}
+}  // namespace re
+
+namespace {
 
 template <class T>
 void dfree(re_ctx* c, T*& p) {
@@ -413,6 +452,7 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
     e.parity_mode = c->opt.pair_parity;
     e.seed = s.seed;
     set_capacity(e, c->opt.nbr_capacity);
+    finish_ens(e);
     if (src) {
       e.cap = (*src)[k]->ens[0].cap;
       for (int q = 0; q < 4; ++q) e.capsub[q] = (*src)[k]->ens[0].capsub[q];
@@ -567,6 +607,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
       e.tau = m.tau;
       e.shift = m.shift;
       e.parity_mode = m.parity_mode;
+      finish_ens(e);
     }
     apply_cells(c, c->opt.cell_div);
     c->cfg = default_cfg(c);

@@ -29,6 +29,20 @@ enum StatusBits : int {
   kStXchg = 32     // not an error: an exchange pattern is waiting at this step boundary
 };
 
+// Per-ensemble step constants, formed once on the host (FP64 transcendentals
+// and divisions run at 1/64 of the FP32 rate on the GPU).  The fields that
+// depend on the thermostat's target T (kbar, af, bf, gf) are filled per
+// replica by set_thermo_target.
+struct StepConst {
+  double lam32, lam64, inv_l, dtq, hdt, inv_hdt, uc, rc2, c_th, kbar;
+  double kbar1, af1, bf1, gf1;  // kbar = kbar1 T, af = af1 T, bf = bf1 sqrt(T), gf = gf1 / sqrt(T)
+  float rc2u, rl2u, half2u, inv_lam2;
+  // thermostat constants of the mixed path (used in FP32): c - 1,
+  // (1 - c) Kbar / Nf, 2 sqrt(c (1 - c) Kbar / Nf), sqrt(c Nf / ((1 - c) Kbar))
+  float cm1f, af, bf, gf;
+  int nf, pad_;
+};
+
 struct EnsDev {
   int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
   int nc, m;                    // list cells per side (0: all pairs), reach in cells
@@ -37,7 +51,17 @@ struct EnsDev {
   int shift, parity_mode, pad_;
   double L, rc, rlist, skin, dt, tau;
   uint64_t seed;
+  StepConst kc;  // filled by finish_ens (host) once the fields above are set
 };
+
+// The constants of StepConst that depend on the target temperature T.
+__host__ __device__ inline void set_thermo_target(StepConst& k, double T) {
+  k.kbar = k.kbar1 * T;
+  k.af = (float)(k.af1 * T);
+  const float ts = sqrtf((float)T);
+  k.bf = (float)k.bf1 * ts;
+  k.gf = (float)k.gf1 / ts;
+}
 
 struct RepDev {
   int ens, id, atom_off, pad_;
@@ -101,6 +125,8 @@ struct LaunchCfg {
 // Host helpers (re_capi.cu): list cells of an ensemble and neighbour capacities.
 void choose_cells(double L, double rlist, int N, int want_m, int* nc_out, int* m_out);
 void set_capacity(EnsDev& e, int user_cap);
+// e.kc from L, rc, rlist, skin, dt, tau, shift and N (target T = 1)
+void finish_ens(EnsDev& e);
 
 // Host-side launchers (re_kernels.cu).  All return the launch status.
 cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,

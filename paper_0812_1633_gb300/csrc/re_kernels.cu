@@ -237,49 +237,6 @@ struct Pos64 {
 };
 
 // ------------------------------------------------------------------ batched
-struct StepConst {
-  double lam32, lam64, inv_l, dtq, hdt, uc, rc2, c_th, kbar;
-  float rc2u, rl2u, half2u, inv_lam2;
-  // thermostat constants of the mixed path (formed in FP64, used in FP32):
-  // c - 1, (1 - c) Kbar / Nf, 2 sqrt(c (1 - c) Kbar / Nf), sqrt(c Nf / ((1 - c) Kbar))
-  float cm1f, af, bf, gf;
-  int nf;
-};
-
-// The constants that depend on the thermostat's target temperature T (they
-// change when an exchange is accepted inside a free-running launch).
-__device__ __forceinline__ void set_thermo_target(StepConst& k, const EnsDev& E, double T) {
-  k.kbar = 0.5 * k.nf * T;
-  const double omc = E.tau > 0.0 ? -expm1(-E.dt / E.tau) : 0.0;  // 1 - c without cancellation
-  k.cm1f = (float)(-omc);
-  k.af = (float)(omc * k.kbar / k.nf);
-  k.bf = (float)(2.0 * sqrt(k.c_th * omc * k.kbar / k.nf));
-  k.gf = omc > 0.0 ? (float)sqrt(k.c_th * k.nf / (omc * k.kbar)) : 0.0f;
-}
-
-__device__ __forceinline__ StepConst step_const(const EnsDev& E, double T) {
-  StepConst k;
-  k.lam32 = E.L * 0x1.0p-32;
-  k.lam64 = E.L * 0x1.0p-64;
-  k.inv_l = 1.0 / E.L;
-  k.dtq = E.dt * 0x1.0p64 / E.L;
-  k.hdt = 0.5 * E.dt;
-  const double rc6 = E.rc * E.rc * E.rc * E.rc * E.rc * E.rc;
-  k.uc = E.shift ? 4.0 * (1.0 / (rc6 * rc6) - 1.0 / rc6) : 0.0;
-  k.rc2 = E.rc * E.rc;
-  const double rcu = E.rc / k.lam32;
-  k.rc2u = (float)(rcu * rcu);
-  const double rlu = E.rlist * (1.0 + 1e-6) / k.lam32;
-  k.rl2u = (float)(rlu * rlu);
-  const double hu = 0.5 * E.skin * (1.0 - 1e-6) / k.lam32;
-  k.half2u = (float)(hu * hu);
-  k.inv_lam2 = (float)(1.0 / (k.lam32 * k.lam32));
-  k.nf = 3 * E.N - 3;
-  k.c_th = E.tau > 0.0 ? exp(-E.dt / E.tau) : 1.0;
-  set_thermo_target(k, E, T);
-  return k;
-}
-
 struct BatchedSmem {
   uint16_t* nb_sm;  // this CTA's neighbour sub-lists when they fit in shared memory
   void* pos;       // uint4[N] (mixed: top 32 bits of x, y, z) or Pos64[N] (fp64)
@@ -388,12 +345,13 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
   uint32_t wofs = col * 4;
   const uint32_t jump = ncols * 4 - 3u;
   int cnt = 0;
+  bool coincident = false;
   auto accept = [&](int j, Hi3 pj) {
     const float r2 = sep2_hi(pi, pj);
     if (j != i && r2 < rl2u) {
       // two distinct atoms at one point (closer than L / 2^32): the pair loop
-      // treats distance 0 as the sub-list padding, so report it here
-      if (r2 == 0.0f) *overflow |= kStNumeric;
+      // treats distance 0 as the sub-list padding, so report it (below)
+      coincident |= (r2 == 0.0f);
       if (cnt < cap_sub) {
         nb[wofs] = (uint16_t)j;
         wofs += ((cnt & 3) == 3) ? jump : 1u;
@@ -407,7 +365,10 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
     const int cx = (int)__umulhi(pi.x, (uint32_t)nc), cy = (int)__umulhi(pi.y, (uint32_t)nc),
               cz = (int)__umulhi(pi.z, (uint32_t)nc);
     // cells z in [cz - m, cz + m] (periodic) are at most two contiguous ranges
-    // of the cell order: [lo1, hi1) and [0, hi2) (empty when hi2 == 0)
+    // of the cell order: [lo1, hi1) and [0, hi2) (empty when hi2 == 0).
+    // (Pruning columns and z ranges to the sphere with the atom's exact offset
+    // scans fewer candidates but was not faster: the per-column work and the
+    // lane divergence it adds cost as much as the candidates it saves.)
     const int zlo = cz - m, zhi = cz + m;
     const int lo1 = zlo < 0 ? zlo + nc : zlo;
     const int hi1 = (zlo < 0 || zhi >= nc) ? nc : zhi + 1;
@@ -440,6 +401,7 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
       }
     }
   }
+  if (coincident) *overflow |= kStNumeric;
   if (cnt > cap_sub) {
     *overflow |= kStOverflow;
     cnt = cap_sub;
@@ -766,7 +728,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const RepDev rd = reps[r];
   if (threadIdx.x == 0) {
     E = ens[rd.ens];
-    K = step_const(E, S.T[r]);
+    K = E.kc;
+    set_thermo_target(K, S.T[r]);
     Tcur_sh = S.T[r];
     A0_sh = S.attempt[rd.ens];
     since_sh = 0;
@@ -1006,7 +969,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         if (!isfinite(kl)) st |= kStNumeric;
         ik = f2ll_split(kl * kEnScale);
       }
-      iu = warp_sum_i64(iu);
+      if (energy) iu = warp_sum_i64(iu);  // U is summed only when it is reported
       ik = warp_sum_i64(ik);
     }
     st = warp_or(st);
@@ -1036,15 +999,15 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     st = 0;
     for (int rk = 0; rk < C; ++rk) st |= sm.slot_st[rk];
   };
-  auto totals_int = [&](long long& iu, long long& ik, int& st) {
+  auto totals_int = [&](long long& iu, long long& ik, int& st, bool energy) {
     const long long* uk = reinterpret_cast<const long long*>(sm.slot_uk);
     long long a = 0, b = 0;
     for (int idx = lane; idx < C * kMaxWarps; idx += 32)
       if (idx % kMaxWarps < nw) {
-        a += uk[idx * 2 + 0];
+        if (energy) a += uk[idx * 2 + 0];
         b += uk[idx * 2 + 1];
       }
-    iu = warp_sum_i64(a);
+    iu = energy ? warp_sum_i64(a) : 0ll;
     ik = warp_sum_i64(b);
     st = 0;
     for (int rk = 0; rk < C; ++rk) st |= sm.slot_st[rk];
@@ -1054,13 +1017,14 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // shared-memory lists: bring this CTA's valid lists in (blocks of four entries)
   const int nblk_sub = cap_sub / 4;
   if (LSM && valid0) {
-    const int cols = per * P;
-    for (int idx = tid; idx < nblk_sub * cols; idx += T) {
-      const int kb = idx / cols, c = idx - kb * cols;
-      if (i0 + c / P < i1)
-        reinterpret_cast<uint2*>(nb)[(size_t)kb * cols + c] =
-            reinterpret_cast<const uint2*>(nbg)[(size_t)kb * N * P + (size_t)i0 * P + c];
-    }
+    // asynchronous copies, all in flight at once (the loop issues, one wait)
+    const int cols = per * P, own_cols = (i1 - i0) * P;
+    uint2* dst = reinterpret_cast<uint2*>(nb);
+    const uint2* src = reinterpret_cast<const uint2*>(nbg) + (size_t)i0 * P;
+    for (int kb = 0; kb < nblk_sub; ++kb)
+      for (int c = tid; c < own_cols; c += T)
+        cp_async8(dst + (size_t)kb * cols + c, src + (size_t)kb * N * P + c);
+    cp_async_wait_all();
     __syncthreads();
   }
 
@@ -1082,7 +1046,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       if (!isfinite(U) || !isfinite(Kin)) status |= kStNumeric;
     } else {
       long long iu, ik;
-      totals_int(iu, ik, status);
+      totals_int(iu, ik, status, true);
       U = 0.5 * (double)iu * kEnUnit;  // FP64 only for the stored energies
       Kin = 0.5 * (double)ik * kEnUnit;
     }
@@ -1136,7 +1100,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     if (mdall > K.half2u) rebuild();
     // the pair energies are summed only when U is reported (the last step;
     // every step in free-running mode, where the last step is not known ahead)
-    forces_and_publish(true, async_nx > 0 || freerun || s + 1 == B, overflow);
+    const bool energy = async_nx > 0 || freerun || s + 1 == B;
+    forces_and_publish(true, energy, overflow);
     // master-stop mode: CTA 0 reads the master's flag and tells every CTA of
     // the cluster (through the status slots) that this step is the last
     if (async_nx > 0 && !is_master && crank == 0 && tid == 0) {
@@ -1202,7 +1167,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       // them after a block barrier (far cheaper than every warp repeating it)
       long long iu = 0, ik = 0;
       if (warp == 0) {
-        totals_int(iu, ik, st);
+        totals_int(iu, ik, st, energy);
         st &= ~(int)kStXchg;
         if (z.bad) st |= kStRngCap;
         const float Kf = ll2f_split(ik) * (float)(0.5 * kEnUnit);
@@ -1250,7 +1215,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           econs += warp_sum(dsum);
           kp = __shfl_sync(0xffffffffu, kp, (slot - fold0) & 31);
           Kin = kp;
-          U = 0.5 * (double)iu * kEnUnit;
+          if (energy) U = 0.5 * (double)iu * kEnUnit;
           __syncwarp();
           if (lane == 0) fold0_sh = slot + 1 == kNoiseChunk ? 0 : slot + 1;
           __syncwarp();
@@ -1309,7 +1274,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       Kin = Ks;
       if (tid == 0) {
         if (Tn != Tcur_sh) {
-          set_thermo_target(K, E, Tn);  // read by others only after the next barriers
+          set_thermo_target(K, Tn);  // read by others only after the next barriers
           Tcur_sh = Tn;
         }
         since_sh = 0;
@@ -1332,13 +1297,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // shared-memory lists go back to global memory for the next launch
   if (LSM) {
     __syncthreads();
-    const int cols = per * P;
-    for (int idx = tid; idx < nblk_sub * cols; idx += T) {
-      const int kb = idx / cols, c = idx - kb * cols;
-      if (i0 + c / P < i1)
-        reinterpret_cast<uint2*>(nbg)[(size_t)kb * N * P + (size_t)i0 * P + c] =
-            reinterpret_cast<const uint2*>(nb)[(size_t)kb * cols + c];
-    }
+    const int cols = per * P, own_cols = (i1 - i0) * P;
+    const uint2* src = reinterpret_cast<const uint2*>(nb);
+    uint2* dst = reinterpret_cast<uint2*>(nbg) + (size_t)i0 * P;
+    for (int kb = 0; kb < nblk_sub; ++kb)
+      for (int c = tid; c < own_cols; c += T) dst[(size_t)kb * N * P + c] = src[(size_t)kb * cols + c];
   }
   // write the state back
   if (own) {
@@ -1353,7 +1316,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         fcomp(S, d)[g] = f[j];
       } else {
         vcomp(S, d)[g] = (double)vq[j] * 0x1.0p-48;
-        fcomp(S, d)[g] = (double)hf[j] / K.hdt;
+        fcomp(S, d)[g] = (double)hf[j] * K.inv_hdt;
       }
     }
     ncnt[(size_t)i * P + q] = cnt;
@@ -1384,7 +1347,7 @@ __global__ void plain_kick_drift(StateDev S, const EnsDev* __restrict__ ens,
   __shared__ float scr[kMaxWarps];
   const RepDev rd = reps[r];
   const EnsDev E = ens[rd.ens];
-  const StepConst K = step_const(E, 1.0);
+  const StepConst& K = E.kc;
   const double vs = S.vscale[r];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float md = 0.0f;
@@ -1418,7 +1381,7 @@ __global__ void plain_rebuild(StateDev S, const EnsDev* __restrict__ ens,
   __shared__ int ovf;
   const RepDev rd = reps[r];
   const EnsDev E = ens[rd.ens];
-  const StepConst K = step_const(E, 1.0);
+  const StepConst& K = E.kc;
   const bool need = !S.valid[r] || __uint_as_float(S.dmax[r]) > K.half2u;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1466,7 +1429,7 @@ __global__ void plain_forces(StateDev S, const EnsDev* __restrict__ ens,
   __shared__ double scr[kMaxWarps];
   const RepDev rd = reps[r];
   const EnsDev E = ens[rd.ens];
-  const StepConst K = step_const(E, 1.0);
+  const StepConst& K = E.kc;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double e = 0.0;
   if (i < E.N) {

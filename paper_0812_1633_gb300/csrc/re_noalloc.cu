@@ -95,6 +95,7 @@ extern "C" int re_lj_forces_device_noalloc(int N, double L, double rc, int shift
   e.tau = 0.0;
   e.shift = shift ? 1 : 0;
   re::set_capacity(e, 0);
+  re::finish_ens(e);
   if (e.capsub[0] > kMaxNeighbours)
     return fail(RE_EOVERFLOW, "density too high for the fixed neighbour capacity (256 per atom)");
   re::choose_cells(L, e.rlist, N, 0, &e.nc, &e.m);
