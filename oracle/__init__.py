@@ -62,6 +62,7 @@ class Rep(C.Structure):
         ("pi", C.POINTER(C.c_int)), ("pj", C.POINTER(C.c_int)),
         ("npairs", C.c_int), ("maxpairs", C.c_int),
         ("list_valid", C.c_int), ("status", C.c_int),
+        ("lam", C.c_double),
     ]
 
 
@@ -105,6 +106,11 @@ def lib():
                                        C.POINTER(C.c_int32), C.POINTER(C.c_uint8), dp]
             L.orc_exchange.restype = C.c_int
             L.orc_apply_exchange.argtypes = [C.POINTER(rp), C.c_int, dp, dp]
+            L.orc_exchange_h.argtypes = [C.c_int, dp, dp, dp, C.c_uint64, C.c_int64, C.c_int,
+                                         C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
+                                         dp, dp]
+            L.orc_exchange_h.restype = C.c_int
+            L.orc_apply_exchange_h.argtypes = [C.POINTER(rp), C.c_int, dp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -215,12 +221,30 @@ def exchange(T, U, seed, attempt, parity_mode=0):
     return T, partner, acc, vs, n
 
 
+def exchange_h(T, lam, U, seed, attempt, parity_mode=0, distance=1):
+    """Generalised exchange (parameters (T, lam), pairs at ladder distance d);
+    returns (T_new, lam_new, partner, accepted, vscale, uscale, n_accepted)."""
+    T = np.array(T, dtype=np.float64)
+    lam = np.ones(len(T)) if lam is None else np.array(lam, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    R = len(T)
+    partner = np.zeros(R, np.int32)
+    acc = np.zeros(R, np.uint8)
+    vs = np.zeros(R)
+    us = np.zeros(R)
+    n = lib().orc_exchange_h(R, _dp(T), _dp(lam), _dp(U), seed & (2**64 - 1), attempt,
+                             parity_mode, distance,
+                             partner.ctypes.data_as(C.POINTER(C.c_int32)),
+                             acc.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(vs), _dp(us))
+    return T, lam, partner, acc, vs, us, n
+
+
 # ------------------------------------------------------------------ replicas
 class Replica:
     """One LJ replica with numpy-owned arrays, stepped by the C oracle."""
 
     def __init__(self, N, L, T, seed, stream, rc=2.5, skin=0.5, dt=0.005, tau=0.5,
-                 shift=1, x=None, v=None, step=0, maxpairs=None):
+                 shift=1, x=None, v=None, step=0, maxpairs=None, lam=1.0):
         self.x = np.zeros((N, 3))
         self.v = np.zeros((N, 3))
         self.f = np.zeros((N, 3))
@@ -241,6 +265,7 @@ class Replica:
         r.x, r.v, r.f, r.xref = _dp(self.x), _dp(self.v), _dp(self.f), _dp(self.xref)
         r.pi, r.pj = _ip(self.pi), _ip(self.pj)
         r.npairs, r.maxpairs, r.list_valid, r.status = 0, maxpairs, 0, 0
+        r.lam = float(lam)
         self.rep = r
         if x is None:
             if lib().orc_init_replica(C.byref(r)) != 0:
@@ -261,7 +286,7 @@ class Replica:
 
     def __getattr__(self, name):
         if name in ("N", "L", "rc", "skin", "dt", "tau", "T", "seed", "stream", "step",
-                    "nrebuild", "U", "K", "econs", "npairs", "status", "shift"):
+                    "nrebuild", "U", "K", "econs", "npairs", "status", "shift", "lam"):
             return getattr(self.__dict__["rep"], name)
         raise AttributeError(name)
 
@@ -274,12 +299,14 @@ class Ensemble:
     """Replicas of one system at different temperatures (one ladder)."""
 
     def __init__(self, N, L, temps, seed, rc=2.5, skin=0.5, dt=0.005, tau=0.5, shift=1,
-                 parity_mode=0):
-        self.reps = [Replica(N, L, float(T), seed, k, rc, skin, dt, tau, shift)
+                 parity_mode=0, lams=None, distance=1):
+        lams = [1.0] * len(temps) if lams is None else lams
+        self.reps = [Replica(N, L, float(T), seed, k, rc, skin, dt, tau, shift, lam=lams[k])
                      for k, T in enumerate(temps)]
         self.seed = seed
         self.attempt = 0
         self.parity_mode = parity_mode
+        self.distance = distance
         R = len(self.reps)
         self._arr = (C.POINTER(Rep) * R)(*[C.pointer(r.rep) for r in self.reps])
 
@@ -290,11 +317,15 @@ class Ensemble:
         ens = cls.__new__(cls)
         rc, skin = kw.get("rc", 2.5), kw.get("skin", 0.5)
         dt, tau, shift = kw.get("dt", 0.005), kw.get("tau", 0.5), kw.get("shift", 1)
-        ens.reps = [Replica(N, L, float(T), seed, k, rc, skin, dt, tau, shift, x=x[k], v=v[k])
+        lams = kw.get("lams")
+        lams = [1.0] * len(temps) if lams is None else lams
+        ens.reps = [Replica(N, L, float(T), seed, k, rc, skin, dt, tau, shift, x=x[k], v=v[k],
+                            lam=lams[k])
                     for k, T in enumerate(temps)]
         ens.seed = seed
         ens.attempt = 0
         ens.parity_mode = kw.get("parity_mode", 0)
+        ens.distance = kw.get("distance", 1)
         ens._arr = (C.POINTER(Rep) * len(ens.reps))(*[C.pointer(r.rep) for r in ens.reps])
         return ens
 
@@ -314,10 +345,14 @@ class Ensemble:
     def energies(self):
         return np.array([r.U for r in self.reps])
 
+    def lams(self):
+        return np.array([r.lam for r in self.reps])
+
     def exchange(self):
         T = self.temps()
         U = self.energies()
-        Tn, partner, acc, vs, n = exchange(T, U, self.seed, self.attempt, self.parity_mode)
-        lib().orc_apply_exchange(self._arr, self.R, _dp(Tn), _dp(vs))
+        Tn, ln, partner, acc, vs, us, n = exchange_h(T, self.lams(), U, self.seed, self.attempt,
+                                                     self.parity_mode, self.distance)
+        lib().orc_apply_exchange_h(self._arr, self.R, _dp(Tn), _dp(ln), _dp(vs), _dp(us))
         self.attempt += 1
         return partner, acc

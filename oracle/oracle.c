@@ -294,9 +294,16 @@ static int rebuild(orc_rep *r) {
   return 0;
 }
 
+/* Forces and potential energy of the replica's Hamiltonian lam U_LJ. */
+static double replica_forces(orc_rep *r) {
+  double U = orc_forces_list(r->N, r->L, r->rc, r->shift, r->x, r->npairs, r->pi, r->pj, r->f);
+  for (int i = 0; i < 3 * r->N; ++i) r->f[i] *= r->lam;
+  return r->lam * U;
+}
+
 int orc_refresh(orc_rep *r) {
   if (rebuild(r)) return -1;
-  r->U = orc_forces_list(r->N, r->L, r->rc, r->shift, r->x, r->npairs, r->pi, r->pj, r->f);
+  r->U = replica_forces(r);
   r->K = orc_kinetic(r->N, r->v);
   return 0;
 }
@@ -340,7 +347,7 @@ static void md_step(orc_rep *r) {
   if (!r->list_valid || maxd2 > half * half) {
     if (rebuild(r)) return;
   }
-  r->U = orc_forces_list(N, r->L, r->rc, r->shift, r->x, r->npairs, r->pi, r->pj, r->f);
+  r->U = replica_forces(r);
   for (int i = 0; i < 3 * N; ++i) r->v[i] += hdt * r->f[i];
   double K = orc_kinetic(N, r->v);
   if (r->tau > 0.0) {
@@ -450,5 +457,100 @@ void orc_apply_exchange(orc_rep **reps, int R, const double *Tnew, const double 
       r->K = Knew;
     }
     r->T = Tnew[k];
+  }
+}
+
+/* ------------------------------------------------ generalised exchange */
+/* The Implementation section's exchange with two extensions it mentions
+ * (non-nearest-neighbour pairs) or allows (parameters other than T): replica
+ * k samples exp(-(K + lam_k U_LJ)/T_k); swapping the parameter sets of a and b
+ * is accepted with min(1, exp(D)), D = (lam_a/T_a - lam_b/T_b)(u_a - u_b),
+ * u = U/lam the unscaled LJ energy (the kinetic part is handled by the
+ * velocity rescaling, as for temperatures). */
+typedef struct { double key; int id; } kk;
+static int cmp_kk(const void *a, const void *b) {
+  const kk *x = (const kk *)a, *y = (const kk *)b;
+  if (x->key < y->key) return -1;
+  if (x->key > y->key) return 1;
+  return x->id - y->id;
+}
+
+int orc_exchange_h(int R, double *T, double *lam, const double *U, uint64_t seed,
+                   int64_t attempt, int parity_mode, int distance, int32_t *partner,
+                   uint8_t *accepted, double *vscale, double *uscale) {
+  const int d = distance < 1 ? 1 : distance;
+  kk *order = (kk *)malloc(sizeof(kk) * (size_t)R);
+  for (int i = 0; i < R; ++i) {
+    order[i].key = T[i] / (lam ? lam[i] : 1.0);
+    order[i].id = i;
+  }
+  qsort(order, (size_t)R, sizeof(kk), cmp_kk);
+  int p;
+  if (parity_mode == 0) {
+    p = (int)(attempt & 1);
+  } else {
+    double u[4];
+    orc_uniform4(seed, ~0ULL, (uint64_t)attempt, ORC_TAG_PARITY, 0, u);
+    p = u[0] < 0.5 ? 0 : 1;
+  }
+  for (int i = 0; i < R; ++i) {
+    partner[i] = -1;
+    accepted[i] = 0;
+    vscale[i] = 1.0;
+    uscale[i] = 1.0;
+  }
+  const int o = p * d;
+  int nacc = 0;
+  for (int q = o; q + d < R; ++q) {
+    if ((q - o) % (2 * d) >= d) continue; /* q is the upper member of a pair */
+    int a = order[q].id, b = order[q + d].id;
+    double Ta = T[a], Tb = T[b];
+    double la = lam ? lam[a] : 1.0, lb = lam ? lam[b] : 1.0;
+    double delta = (la / Ta - lb / Tb) * (U[a] / la - U[b] / lb);
+    int lo = a < b ? a : b;
+    double u[4];
+    orc_uniform4(seed, (uint64_t)lo, (uint64_t)attempt, ORC_TAG_EXCH, 0, u);
+    int ok = (delta >= 0.0) || (u[0] < exp(delta));
+    partner[a] = b;
+    partner[b] = a;
+    if (ok) {
+      accepted[a] = accepted[b] = 1;
+      vscale[a] = sqrt(Tb / Ta);
+      vscale[b] = sqrt(Ta / Tb);
+      uscale[a] = lb / la;
+      uscale[b] = la / lb;
+      T[a] = Tb;
+      T[b] = Ta;
+      if (lam) {
+        lam[a] = lb;
+        lam[b] = la;
+      }
+      ++nacc;
+    }
+  }
+  free(order);
+  return nacc;
+}
+
+void orc_apply_exchange_h(orc_rep **reps, int R, const double *Tnew, const double *lamnew,
+                          const double *vscale, const double *uscale) {
+  for (int k = 0; k < R; ++k) {
+    orc_rep *r = reps[k];
+    double s = vscale[k];
+    if (s != 1.0) {
+      for (int i = 0; i < 3 * r->N; ++i) r->v[i] *= s;
+      double Knew = r->K * (s * s);
+      r->econs += r->K - Knew;
+      r->K = Knew;
+    }
+    double us = uscale[k];
+    if (us != 1.0) {
+      for (int i = 0; i < 3 * r->N; ++i) r->f[i] *= us;
+      double Unew = r->U * us;
+      r->econs += r->U - Unew;
+      r->U = Unew;
+    }
+    r->T = Tnew[k];
+    r->lam = lamnew[k];
   }
 }

@@ -46,6 +46,7 @@ typedef struct orc_rep {
   int npairs, maxpairs;
   int list_valid;
   int status;                     /* 0 ok, -1 list overflow */
+  double lam;                     /* potential scale: the replica's Hamiltonian is K + lam U_LJ */
 } orc_rep;
 
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
@@ -95,6 +96,21 @@ int orc_exchange(int R, double *T, const double *U, uint64_t seed, int64_t attem
                  int parity_mode, int32_t *partner, uint8_t *accepted, double *vscale);
 /* Apply an exchange to replica states: scale v, update T, K and econs. */
 void orc_apply_exchange(orc_rep **reps, int R, const double *Tnew, const double *vscale);
+
+/* Generalised (Hamiltonian) exchange with pairs at ladder distance
+ * `distance`: replica k has parameters (T_k, lam_k) and potential energy
+ * U_k = lam_k U_LJ(x_k).  Ladder order = ascending T/lam; pairs (q, q + d)
+ * for q - o in [0, d) mod 2d, o = p d with p the parity offset;
+ * D = (lam_a/T_a - lam_b/T_b)(U_a/lam_a - U_b/lam_b); on acceptance the pair
+ * swaps (T, lam), vscale = sqrt(T_new/T_old), uscale = lam_new/lam_old.
+ * lam NULL: all 1 (then identical to orc_exchange when distance == 1). */
+int orc_exchange_h(int R, double *T, double *lam, const double *U, uint64_t seed,
+                   int64_t attempt, int parity_mode, int distance, int32_t *partner,
+                   uint8_t *accepted, double *vscale, double *uscale);
+/* Applies an exchange to the replicas: v *= vscale (K and econs follow),
+ * f *= uscale and U *= uscale (econs absorbs the change of U), new T, lam. */
+void orc_apply_exchange_h(orc_rep **reps, int R, const double *Tnew, const double *lamnew,
+                          const double *vscale, const double *uscale);
 
 #ifdef __cplusplus
 }

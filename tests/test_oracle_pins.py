@@ -441,3 +441,122 @@ def test_budgets_are_per_replica_and_thread_independent():
     for ra, rb, s in zip(a.reps, b.reps, [5, 17, 0]):
         assert ra.step == s
         assert np.array_equal(ra.x, rb.x) and np.array_equal(ra.v, rb.v)
+
+
+# ------------------------------------------- generalised (Hamiltonian) exchange
+def test_generalised_exchange_reduces_to_temperature_exchange():
+    rng = np.random.default_rng(3)
+    for R in (2, 5, 9):
+        for att in range(12):
+            T = rng.permutation(0.7 * 1.03 ** np.arange(R))
+            U = rng.normal(-4000, 40, R)
+            a = O.exchange(T, U, 77, att, att % 2)
+            b = O.exchange_h(T, None, U, 77, att, att % 2, 1)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[2])
+            assert np.array_equal(a[2], b[3]) and np.array_equal(a[3], b[4])
+            assert np.array_equal(b[1], np.ones(R)) and np.array_equal(b[5], np.ones(R))
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_distance_d_pattern(d):
+    rng = np.random.default_rng(d)
+    R = 11
+    ladder = 0.7 * 1.0275 ** np.arange(R)
+    T = rng.permutation(ladder)
+    for att in range(8):
+        U = rng.normal(-5000, 30, R)
+        rank = np.argsort(np.argsort(T))   # ladder position of every replica
+        order = np.argsort(T)
+        Tn, _, partner, acc, _, _, n = O.exchange_h(T, None, U, 1, att, 0, d)
+        o = (att & 1) * d
+        # expected pairs written out: blocks of 2d from offset o, (q, q + d)
+        want = [(order[q], order[q + d]) for q in range(o, R - d) if (q - o) % (2 * d) < d]
+        assert int((partner >= 0).sum()) == 2 * len(want)
+        for a, b in want:
+            assert partner[a] == b and partner[b] == a
+            assert abs(int(rank[a]) - int(rank[b])) == d
+        assert sorted(Tn) == sorted(ladder)
+        T = Tn
+
+
+def test_lambda_exchange_hand_cases():
+    """Equal temperatures, potential scales 1 and 0.5: D = (1 - 0.5)/T (u_a - u_b),
+    u = U/lam; the lower id's uniform decides."""
+    seed, att, T = 13, 0, 1.5
+    r0 = O.uniform4(seed, 0, att, O.TAG_EXCH)[0]
+    lam = [1.0, 0.5]
+    # ladder order by T/lam: replica 0 (1.5) before replica 1 (3.0)
+    for D, want in [(math.log(r0) + 1e-9, 1), (math.log(r0) - 1e-9, 0), (0.3, 1)]:
+        ub = -100.0
+        ua = ub + D * T / 0.5         # (1/T - 0.5/T) (ua - ub) = D
+        U = [1.0 * ua, 0.5 * ub]       # stored energies are lam * u
+        Tn, ln, partner, acc, vs, us, n = O.exchange_h([T, T], lam, U, seed, att)
+        assert list(partner) == [1, 0] and n == want
+        if want:
+            assert list(ln) == [0.5, 1.0] and list(us) == [0.5, 2.0]
+            assert list(vs) == [1.0, 1.0] and list(Tn) == [T, T]
+        else:
+            assert list(ln) == lam and list(us) == [1.0, 1.0]
+
+
+@pytest.mark.parametrize("D", [-0.3, -1.5])
+def test_lambda_acceptance_frequency_is_metropolis(D):
+    n, T = 20000, 1.0
+    lam = [1.0, 0.6]
+    ub = -50.0
+    ua = ub + D * T / (1.0 - 0.6)
+    U = [ua, 0.6 * ub]
+    acc = sum(O.exchange_h([T, T], lam, U, 31, a)[6] for a in range(0, 2 * n, 2))
+    p = math.exp(D)
+    assert abs(acc / n - p) < 3 * math.sqrt(p * (1 - p) / n)
+
+
+def test_lambda_scales_forces_and_energy():
+    # two atoms: closed-form pair force and energy, scaled by lam
+    L, r = 10.0, 1.3
+    x = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+    v = np.zeros((2, 3))
+    a = O.Replica(2, L, 1.0, 1, 0, x=x, v=v)
+    b = O.Replica(2, L, 1.0, 1, 0, x=x, v=v, lam=0.37)
+    uc = 4.0 * (2.5 ** -12 - 2.5 ** -6)
+    u = 4.0 * (r ** -12 - r ** -6) - uc
+    fx = 24.0 * (2.0 * r ** -13 - r ** -7)
+    assert a.U == pytest.approx(u, rel=1e-14) and b.U == pytest.approx(0.37 * u, rel=1e-14)
+    assert b.f[1, 0] == pytest.approx(0.37 * fx, rel=1e-13) and b.f[0, 0] == -b.f[1, 0]
+    # a liquid: every force component scales
+    xs, Lb = melted(108, seed=2, amp=0.12)
+    vs = O.init_velocities(108, 1.0, 1, 0)
+    p = O.Replica(108, Lb, 1.0, 1, 0, x=xs, v=vs)
+    q = O.Replica(108, Lb, 1.0, 1, 0, x=xs, v=vs, lam=0.8)
+    assert np.allclose(q.f, 0.8 * p.f, rtol=1e-14, atol=0) and q.U == pytest.approx(0.8 * p.U)
+
+
+def test_lambda_nve_conserves_scaled_hamiltonian():
+    N = 108
+    x, L = melted(N, seed=4, amp=0.1)
+    v = O.init_velocities(N, 1.0, 2, 0)
+    r = O.Replica(N, L, 1.0, 1, 0, tau=0.0, dt=0.002, x=x, v=v, lam=0.7)
+    H0 = r.U + r.K
+    for _ in range(20):
+        r.steps(10)
+        assert abs(r.U + r.K - H0) / N < 2e-4
+
+
+def test_lambda_swap_keeps_effective_energy():
+    N = 32
+    L = box(N) * 1.3
+    ens = O.Ensemble(N, L, [1.0, 1.0], seed=3, tau=0.5, lams=[1.0, 0.5])
+    ens.advance([20, 20])
+    f0 = [r.f.copy() for r in ens.reps]
+    H0 = [r.H for r in ens.reps]
+    # force acceptance: u0 well above u1 makes D = (1 - 0.5)(u0 - u1) > 0
+    ens.reps[0].rep.U, ens.reps[1].rep.U = 0.0, 0.5 * -100.0
+    H0 = [0.0 + ens.reps[0].K + ens.reps[0].econs, -50.0 + ens.reps[1].K + ens.reps[1].econs]
+    partner, acc = ens.exchange()
+    assert list(acc) == [1, 1]
+    assert ens.lams().tolist() == [0.5, 1.0] and ens.temps().tolist() == [1.0, 1.0]
+    assert np.allclose(ens.reps[0].f, 0.5 * f0[0], rtol=1e-15, atol=0)
+    assert np.allclose(ens.reps[1].f, 2.0 * f0[1], rtol=1e-15, atol=0)
+    assert ens.reps[1].U == pytest.approx(-100.0)
+    for r, h in zip(ens.reps, H0):
+        assert r.H == pytest.approx(h, rel=1e-12)   # econs absorbs the change of U
