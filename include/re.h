@@ -79,6 +79,10 @@ typedef struct re_opts {
                        every this many steps (0: every 200; < 0: never).  Results
                        differ only in summation order; atom order in the API is
                        always the original one. */
+  int exch_distance;/* exchange pairs at ladder distance d (default 1: nearest
+                       neighbours).  Non-nearest exchanges are the extension the
+                       Implementation section mentions: positions (q, q + d) in
+                       blocks of 2d, offset by d on odd attempts (parity). */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -93,6 +97,19 @@ void re_default_opts(re_opts *o);
  * batched path.  *out receives the new context. */
 int re_create(int N, double L, double rc, int n_rep, const double *temps, uint64_t seed,
               const re_opts *opt, re_ctx **out);
+
+/* Generalised (Hamiltonian) replica exchange: as re_create, and replica k
+ * also carries a potential scale lams[k] > 0 (host; NULL: all 1), so that its
+ * Hamiltonian is K + lams[k] U_LJ (forces and reported U scale by lams[k]).
+ * Exchanges then swap the parameter sets (T, lam): the ladder is ordered by
+ * T/lam (keys must be distinct), D = (lam_a/T_a - lam_b/T_b)(U_a/lam_a -
+ * U_b/lam_b), and on acceptance velocities scale by sqrt(T_new/T_old) and
+ * forces and U by lam_new/lam_old (econs absorbs the jump, so H~ stays
+ * continuous).  lam = 1 everywhere is the paper's temperature exchange.  The
+ * paper implements temperatures only; it states the scheme extends to other
+ * exchanges. */
+int re_create_h(int N, double L, double rc, int n_rep, const double *temps, const double *lams,
+                uint64_t seed, const re_opts *opt, re_ctx **out);
 
 /* Builds one context holding the replicas of n contexts (ensembles of uneven
  * sizes), so that one launch advances all of them.  The members are copied;
@@ -165,6 +182,8 @@ int re_run(re_ctx *c, int n_cycles, const int32_t *steps, int use_graph);
 int re_energies(re_ctx *c, double *U, double *K, double *H);
 /* Current temperature of every replica (host, n_rep). */
 int re_temps(re_ctx *c, double *T);
+/* Potential scale lam of every replica id (host, n_rep values). */
+int re_lambdas(re_ctx *c, double *lam);
 /* Positions (wrapped into [0, L)) and velocities, host arrays of
  * 3 * (atoms of all replicas) doubles each; either may be NULL. */
 int re_get_state(re_ctx *c, double *x, double *v);
@@ -208,6 +227,17 @@ void re_destroy(re_ctx *c);
 int re_exchange_device(int R, const double *T, const double *U, uint64_t seed, int64_t attempt,
                        int parity_mode, double *T_out, int32_t *partner, uint8_t *accepted,
                        double *vscale, void *stream);
+
+/* re_exchange_device generalised like re_create_h: lam (device, R values,
+ * NULL: all 1) and pairs at ladder distance `distance` (>= 1).  Outputs as
+ * re_exchange_device, plus lam_out (NULL allowed) = the swapped scales and
+ * uscale (NULL allowed) = lam_new/lam_old per replica.  Keys T/lam must be
+ * distinct and positive.  The same decisions as re_exchange for the same
+ * state. */
+int re_exchange_device_h(int R, const double *T, const double *lam, const double *U,
+                         uint64_t seed, int64_t attempt, int parity_mode, int distance,
+                         double *T_out, double *lam_out, int32_t *partner, uint8_t *accepted,
+                         double *vscale, double *uscale, void *stream);
 
 /* Truncated LJ forces and potential energy of N atoms in a cubic periodic box
  * of side L with cutoff rc (Example section): x device array of 3N doubles

@@ -34,7 +34,7 @@ class _Opts(C.Structure):
                 ("shift_energy", C.c_int), ("precision", C.c_int), ("path", C.c_int),
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
                 ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int),
-                ("sort_interval", C.c_int)]
+                ("sort_interval", C.c_int), ("exch_distance", C.c_int)]
 
 
 _lib = None
@@ -54,6 +54,8 @@ def lib():
         L.re_default_opts.restype = None
         L.re_create.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, dp, C.c_uint64,
                                 C.POINTER(_Opts), C.POINTER(vp)]
+        L.re_create_h.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, C.c_uint64,
+                                  C.POINTER(_Opts), C.POINTER(vp)]
         L.re_group.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
         L.re_advance.argtypes = [vp, i32p]
         L.re_exchange.argtypes = [vp, i32p, u8p]
@@ -65,6 +67,7 @@ def lib():
                                   C.POINTER(C.c_uint8)]
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
+        L.re_lambdas.argtypes = [vp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
         L.re_set_state.argtypes = [vp, dp, dp]
         L.re_forces.argtypes = [vp, dp]
@@ -82,6 +85,8 @@ def lib():
         L.re_destroy.restype = None
         L.re_exchange_device.argtypes = [C.c_int, vp, vp, C.c_uint64, C.c_int64, C.c_int, vp, vp,
                                          vp, vp, vp]
+        L.re_exchange_device_h.argtypes = [C.c_int, vp, vp, vp, C.c_uint64, C.c_int64, C.c_int,
+                                           C.c_int, vp, vp, vp, vp, vp, vp, vp]
         L.re_lj_forces_device.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, vp,
                                           vp, vp, vp]
         L.re_lj_forces_device_noalloc.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, vp, vp,
@@ -112,7 +117,8 @@ class Context:
 
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
-                 cell_div=0, cluster=0, atom_threads=0, sort_interval=0, _handle=None):
+                 cell_div=0, cluster=0, atom_threads=0, sort_interval=0, lam=None,
+                 exch_distance=1, _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -125,9 +131,14 @@ class Context:
             o.pair_parity, o.nx, o.nbr_capacity = pair_parity, nx, nbr_capacity
             o.cell_div, o.cluster, o.atom_threads = cell_div, cluster, atom_threads
             o.sort_interval = sort_interval
+            o.exch_distance = exch_distance
             t = np.ascontiguousarray(temps, dtype=np.float64)
-            _check(lib().re_create(int(N), float(L), float(rc), len(t), _p(t, C.c_double),
-                                   int(seed) & (2**64 - 1), C.byref(o), C.byref(self._h)))
+            lp = None
+            if lam is not None:
+                lam = np.ascontiguousarray(lam, dtype=np.float64)
+                lp = _p(lam, C.c_double)
+            _check(lib().re_create_h(int(N), float(L), float(rc), len(t), _p(t, C.c_double), lp,
+                                     int(seed) & (2**64 - 1), C.byref(o), C.byref(self._h)))
         n_rep, n_ens, n_pairs = C.c_int(), C.c_int(), C.c_int()
         n_atoms = C.c_int64()
         lib().re_info(self._h, C.byref(n_rep), C.byref(n_atoms), C.byref(n_ens), C.byref(n_pairs))
@@ -222,6 +233,11 @@ class Context:
         _check(lib().re_temps(self._h, _p(T, C.c_double)), self._h)
         return T
 
+    def lambdas(self):
+        lam = np.zeros(self.n_rep)
+        _check(lib().re_lambdas(self._h, _p(lam, C.c_double)), self._h)
+        return lam
+
     def get_state(self):
         x = np.zeros((self.n_atoms, 3))
         v = np.zeros((self.n_atoms, 3))
@@ -290,6 +306,27 @@ def exchange_device(T, U, seed, attempt, parity_mode=0, stream=None):
                                     partner.data_ptr(), acc.data_ptr(), vs.data_ptr(),
                                     C.c_void_p(st)))
     return T_out, partner, acc, vs
+
+
+def exchange_device_h(T, lam, U, seed, attempt, parity_mode=0, distance=1, stream=None):
+    """Generalised exchange on device tensors (lam may be None: all 1).
+
+    Returns (T_new, lam_new, partner, accepted, vscale, uscale) as CUDA tensors."""
+    import torch
+    R = T.numel()
+    T_out = torch.empty_like(T)
+    lam_out = torch.empty_like(T)
+    partner = torch.empty(R, dtype=torch.int32, device=T.device)
+    acc = torch.empty(R, dtype=torch.uint8, device=T.device)
+    vs = torch.empty_like(T)
+    us = torch.empty_like(T)
+    st = stream if stream is not None else torch.cuda.current_stream(T.device).cuda_stream
+    _check(lib().re_exchange_device_h(R, T.data_ptr(), None if lam is None else lam.data_ptr(),
+                                      U.data_ptr(), int(seed) & (2**64 - 1), int(attempt),
+                                      int(parity_mode), int(distance), T_out.data_ptr(),
+                                      lam_out.data_ptr(), partner.data_ptr(), acc.data_ptr(),
+                                      vs.data_ptr(), us.data_ptr(), C.c_void_p(st)))
+    return T_out, lam_out, partner, acc, vs, us
 
 
 def lj_forces_device(x, L, rc=2.5, shift=True, precision="fp64", stream=None):

@@ -201,6 +201,7 @@ void finish_ens(EnsDev& e) {
   k.bf1 = 2.0 * std::sqrt(0.5 * k.c_th * omc);
   k.gf1 = omc > 0.0 ? std::sqrt(2.0 * k.c_th / omc) : 0.0;
   set_thermo_target(k, 1.0);
+  set_potential_scale(k, 1.0);
 }
 }  // namespace re
 
@@ -273,6 +274,7 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &s.ncnt, 8 * A)) || (rc = dalloc(c, &s.nbr, (size_t)c->n_nbr)) ||
       (rc = dalloc(c, &s.T, R)) || (rc = dalloc(c, &s.U, R)) || (rc = dalloc(c, &s.K, R)) ||
       (rc = dalloc(c, &s.econs, R)) || (rc = dalloc(c, &s.vscale, R)) ||
+      (rc = dalloc(c, &s.lam, R)) || (rc = dalloc(c, &s.fscale, R)) ||
       (rc = dalloc(c, &s.step, R)) || (rc = dalloc(c, &s.nreb, R)) ||
       (rc = dalloc(c, &s.status, R)) || (rc = dalloc(c, &s.valid, R)) ||
       (rc = dalloc(c, &s.attempt, E)) || (rc = dalloc(c, &s.pair_att, (size_t)c->n_pairs)) ||
@@ -292,6 +294,12 @@ int allocate(re_ctx* c) {
   RE_CUDA(c, cudaMemsetAsync(s.pair_att, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.pair_acc, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.dmax, 0, sizeof(uint32_t) * R, c->stream), "memset");
+  {
+    // potential scales 1 (plain LJ) until re_create_h sets them; no pending force factor
+    const std::vector<double> ones(R, 1.0);
+    RE_CUDA(c, cudaMemcpy(s.lam, ones.data(), 8 * R, cudaMemcpyHostToDevice), "init lam");
+    RE_CUDA(c, cudaMemcpy(s.fscale, ones.data(), 8 * R, cudaMemcpyHostToDevice), "init fscale");
+  }
   RE_CUDA(c, cudaMallocHost(&c->h_ring, sizeof(int32_t) * R * kRing), "cudaMallocHost");
   for (int k = 0; k < kRing; ++k)
     RE_CUDA(c, cudaEventCreateWithFlags(&c->ring_ev[k], cudaEventDisableTiming), "event");
@@ -450,6 +458,7 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
     e.tau = c->opt.tau_T;
     e.shift = c->opt.shift_energy ? 1 : 0;
     e.parity_mode = c->opt.pair_parity;
+    e.xdist = std::max(1, c->opt.exch_distance);
     e.seed = s.seed;
     set_capacity(e, c->opt.nbr_capacity);
     finish_ens(e);
@@ -512,10 +521,16 @@ void re_default_opts(re_opts* o) {
   o->cluster = 0;
   o->atom_threads = 0;
   o->sort_interval = 0;
+  o->exch_distance = 1;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
               const re_opts* opt, re_ctx** out) {
+  return re_create_h(N, L, rc, n_rep, temps, nullptr, seed, opt, out);
+}
+
+int re_create_h(int N, double L, double rc, int n_rep, const double* temps, const double* lams,
+                uint64_t seed, const re_opts* opt, re_ctx** out) {
   g_create_error.clear();
   if (!out) return fail(nullptr, RE_EINVAL, "out is NULL");
   *out = nullptr;
@@ -539,10 +554,17 @@ int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64
     return fail(nullptr, RE_EINVAL, "unknown path %d", o.path);
   if (o.path == RE_PATH_PLAIN) o.precision = RE_PREC_FP64;
   if (o.nx < 0) return fail(nullptr, RE_EINVAL, "nx must be >= 0");
+  if (o.exch_distance < 0) return fail(nullptr, RE_EINVAL, "exch_distance must be >= 1");
   for (int i = 0; i < n_rep; ++i) {
-    if (!(temps[i] > 0)) return fail(nullptr, RE_EINVAL, "temperatures must be positive");
+    if (!(temps[i] > 0) || !std::isfinite(temps[i]))
+      return fail(nullptr, RE_EINVAL, "temperatures must be positive");
+    if (lams && !(lams[i] > 0 && std::isfinite(lams[i])))
+      return fail(nullptr, RE_EINVAL, "potential scales must be positive");
+    const double ki = temps[i] / (lams ? lams[i] : 1.0);
     for (int j = 0; j < i; ++j)
-      if (temps[i] == temps[j]) return fail(nullptr, RE_EINVAL, "temperatures must be distinct");
+      if (ki == temps[j] / (lams ? lams[j] : 1.0))
+        return fail(nullptr, RE_EINVAL, lams ? "ladder keys T/lam must be distinct"
+                                             : "temperatures must be distinct");
   }
   re_ctx* c = new re_ctx();
   c->opt = o;
@@ -552,6 +574,10 @@ int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64
   if (rcode == RE_OK) {
     cudaError_t ce = cudaMemcpyAsync(c->s.T, temps, sizeof(double) * n_rep,
                                      cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess && lams)
+      ce = cudaMemcpyAsync(c->s.lam, lams, sizeof(double) * n_rep, cudaMemcpyHostToDevice,
+                           c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) rcode = cuda_fail(c, ce, "upload temps");
   }
   if (rcode == RE_OK) {
@@ -607,6 +633,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
       e.tau = m.tau;
       e.shift = m.shift;
       e.parity_mode = m.parity_mode;
+      e.xdist = m.xdist;
       finish_ens(e);
     }
     apply_cells(c, c->opt.cell_div);
@@ -639,6 +666,8 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
     cp(c->s.K + r0, s->s.K, 8 * R);
     cp(c->s.econs + r0, s->s.econs, 8 * R);
     cp(c->s.vscale + r0, s->s.vscale, 8 * R);
+    cp(c->s.lam + r0, s->s.lam, 8 * R);
+    cp(c->s.fscale + r0, s->s.fscale, 8 * R);
     cp(c->s.step + r0, s->s.step, 8 * R);
     cp(c->s.nreb + r0, s->s.nreb, 8 * R);
     cp(c->s.status + r0, s->s.status, 4 * R);
@@ -715,7 +744,7 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
   if (!c->d_fr_words) {
     int rc;
     if ((rc = dalloc(c, &c->d_fr_words, (size_t)2 * E + 5 * (size_t)R)) ||
-        (rc = dalloc(c, &c->d_fr_slot, 2 * (size_t)R)))
+        (rc = dalloc(c, &c->d_fr_slot, 4 * (size_t)R)))
       return rc;
   }
   if (want_log && c->log_rows < n_att) {
@@ -743,6 +772,7 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
   fr.flag = fr.done + R;
   fr.order = fr.flag + R;
   fr.slot = c->d_fr_slot;
+  fr.key = c->d_fr_slot + 3 * (size_t)R;
   fr.log_step = c->d_log_step;
   fr.log_T = c->d_log_T;
   fr.log_partner = c->d_log_partner;
@@ -939,6 +969,14 @@ int re_energies(re_ctx* c, double* U, double* K, double* H) {
   return RE_OK;
 }
 
+int re_lambdas(re_ctx* c, double* lam) {
+  if (!c || !lam) return fail(c, RE_EINVAL, "bad arguments");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  RE_CUDA(c, cudaMemcpy(lam, c->s.lam, sizeof(double) * c->n_rep, cudaMemcpyDeviceToHost),
+          "read lam");
+  return RE_OK;
+}
+
 int re_temps(re_ctx* c, double* T) {
   if (!c || !T) return fail(c, RE_EINVAL, "bad arguments");
   RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
@@ -993,8 +1031,11 @@ int re_forces(re_ctx* c, double* f) {
   if (!c || !f) return fail(c, RE_EINVAL, "bad arguments");
   int rc = status_check(c);
   if (rc) return rc;
-  cudaError_t e = re::launch_export_state(c->s, c->d_ens, c->d_rep, c->n_rep, nullptr, nullptr,
-                                          c->d_io, c->stream);
+  // pending velocity and force factors of the last exchange become part of the state
+  cudaError_t e = re::launch_apply_vscale(c->s, c->d_rep, c->d_ens, c->n_rep, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply pending factors");
+  e = re::launch_export_state(c->s, c->d_ens, c->d_rep, c->n_rep, nullptr, nullptr, c->d_io,
+                              c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "export");
   RE_CUDA(c, cudaMemcpyAsync(f, c->d_io, 8 * 3 * (size_t)c->n_atoms, cudaMemcpyDeviceToHost,
                              c->stream), "read f");
@@ -1062,7 +1103,8 @@ int re_autotune(re_ctx* c, int steps) {
       {c->s.qx, 8 * A}, {c->s.qy, 8 * A}, {c->s.qz, 8 * A}, {c->s.vx, 8 * A},
       {c->s.vy, 8 * A}, {c->s.vz, 8 * A}, {c->s.fx, 8 * A}, {c->s.fy, 8 * A},
       {c->s.fz, 8 * A}, {c->s.U, 8 * R},  {c->s.K, 8 * R},  {c->s.econs, 8 * R},
-      {c->s.vscale, 8 * R}, {c->s.step, 8 * R}, {c->s.nreb, 8 * R}, {c->s.status, 4 * R}};
+      {c->s.vscale, 8 * R}, {c->s.fscale, 8 * R}, {c->s.step, 8 * R}, {c->s.nreb, 8 * R},
+      {c->s.status, 4 * R}};
   for (auto& b : bufs) {
     b.save = nullptr;
     cudaError_t e = cudaMalloc(&b.save, b.bytes);
@@ -1192,8 +1234,26 @@ int re_exchange_device(int R, const double* T, const double* U, uint64_t seed, i
   if (!T || !U || !T_out || !partner || !accepted || !vscale)
     return fail(nullptr, RE_EINVAL, "NULL device pointer");
   if (parity_mode != 0 && parity_mode != 1) return fail(nullptr, RE_EINVAL, "parity_mode 0 or 1");
-  cudaError_t e = re::launch_exchange_raw(R, T, U, seed, attempt, parity_mode, T_out, partner,
-                                          accepted, vscale, static_cast<cudaStream_t>(stream));
+  cudaError_t e = re::launch_exchange_raw(R, T, nullptr, U, seed, attempt, parity_mode, 1, T_out,
+                                          nullptr, partner, accepted, vscale, nullptr,
+                                          static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "exchange launch");
+  return RE_OK;
+}
+
+int re_exchange_device_h(int R, const double* T, const double* lam, const double* U,
+                         uint64_t seed, int64_t attempt, int parity_mode, int distance,
+                         double* T_out, double* lam_out, int32_t* partner, uint8_t* accepted,
+                         double* vscale, double* uscale, void* stream) {
+  g_create_error.clear();
+  if (R < 1 || R > 4096) return fail(nullptr, RE_EINVAL, "R must be in [1, 4096]");
+  if (!T || !U || !T_out || !partner || !accepted || !vscale)
+    return fail(nullptr, RE_EINVAL, "NULL device pointer");
+  if (parity_mode != 0 && parity_mode != 1) return fail(nullptr, RE_EINVAL, "parity_mode 0 or 1");
+  if (distance < 1) return fail(nullptr, RE_EINVAL, "distance must be >= 1");
+  cudaError_t e = re::launch_exchange_raw(R, T, lam, U, seed, attempt, parity_mode, distance, T_out,
+                                          lam_out, partner, accepted, vscale, uscale,
+                                          static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "exchange launch");
   return RE_OK;
 }

@@ -36,6 +36,8 @@ enum StatusBits : int {
 struct StepConst {
   double lam32, lam64, inv_l, dtq, hdt, inv_hdt, uc, rc2, c_th, kbar;
   double kbar1, af1, bf1, gf1;  // kbar = kbar1 T, af = af1 T, bf = bf1 sqrt(T), gf = gf1 / sqrt(T)
+  double lamv;                  // the replica's potential scale (set_potential_scale)
+  float hlf;                    // FP32 half-kick factor per force unit, times lamv
   float rc2u, rl2u, half2u, inv_lam2;
   // thermostat constants of the mixed path (used in FP32): c - 1,
   // (1 - c) Kbar / Nf, 2 sqrt(c (1 - c) Kbar / Nf), sqrt(c Nf / ((1 - c) Kbar))
@@ -48,11 +50,18 @@ struct EnsDev {
   int nc, m;                    // list cells per side (0: all pairs), reach in cells
   int cap;                      // neighbour entries per atom: max over P of P * capsub[P]
   int capsub[4];                // sub-list capacity (multiple of 4) for P = 1, 2, 4, 8
-  int shift, parity_mode, pad_;
+  int shift, parity_mode, xdist;  // xdist: exchange pairs at ladder distance xdist (>= 1)
   double L, rc, rlist, skin, dt, tau;
   uint64_t seed;
   StepConst kc;  // filled by finish_ens (host) once the fields above are set
 };
+
+// The constants of StepConst that depend on the replica's potential scale
+// (its Hamiltonian is K + lam U_LJ: forces and U scale by lam).
+__host__ __device__ inline void set_potential_scale(StepConst& k, double lam) {
+  k.lamv = lam;
+  k.hlf = (float)(k.hdt * k.lam32 * lam);
+}
 
 // The constants of StepConst that depend on the target temperature T.
 __host__ __device__ inline void set_thermo_target(StepConst& k, double T) {
@@ -75,6 +84,7 @@ struct StateDev {
   int32_t* ncnt;
   uint16_t* nbr;
   double *T, *U, *K, *econs, *vscale;
+  double *lam, *fscale;  // per replica: potential scale; pending force factor (null: 1)
   int64_t *step, *nreb;
   int32_t *status, *valid;
   int64_t* attempt;                  // per ensemble
@@ -110,7 +120,8 @@ struct FreeDev {
   int32_t* done;     // [Rtot]
   int32_t* flag;     // [Rtot]
   int32_t* order;    // [Rtot] scratch of the master (sorted order, at the ensemble's rep_off)
-  double* slot;      // [2 Rtot] published (T, U)
+  double* slot;      // [3 Rtot] published (T, U, lam)
+  double* key;       // [Rtot] scratch of the master (ladder keys T/lam)
   int64_t* log_step;    // [log_cap x rtot]
   double* log_T;        // [log_cap x rtot]
   int32_t* log_partner; // [log_cap x rtot]
@@ -170,9 +181,10 @@ cudaError_t launch_identity_perm(const StateDev& s, const EnsDev* d_ens, const R
 cudaError_t launch_spatial_sort(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                 int n_rep, int max_n, int max_ncell, int64_t n_atoms,
                                 cudaStream_t st);
-cudaError_t launch_exchange_raw(int R, const double* T, const double* U, uint64_t seed,
-                                int64_t attempt, int parity_mode, double* T_out,
-                                int32_t* partner, uint8_t* accepted, double* vscale,
+cudaError_t launch_exchange_raw(int R, const double* T, const double* lam, const double* U,
+                                uint64_t seed, int64_t attempt, int parity_mode, int distance,
+                                double* T_out, double* lam_out, int32_t* partner,
+                                uint8_t* accepted, double* vscale, double* uscale,
                                 cudaStream_t st);
 
 }  // namespace re

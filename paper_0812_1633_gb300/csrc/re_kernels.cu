@@ -99,6 +99,7 @@ __global__ void init_lattice_kernel(StateDev S, const EnsDev* __restrict__ ens,
     S.U[r] = 0.0;
     S.econs[r] = 0.0;
     S.vscale[r] = 1.0;
+    S.fscale[r] = 1.0;
     S.step[r] = 0;
     S.nreb[r] = 0;
     S.status[r] = 0;
@@ -558,15 +559,28 @@ __device__ __forceinline__ long long warp_sum_i64(long long v) {
   return v;
 }
 
-// Metropolis rule of the Implementation section for the pair (a colder, b
-// hotter): D = (1/T_a - 1/T_b)(U_a - U_b); accept iff D >= 0 or r < exp(D),
-// r the uniform of the lower replica id for this attempt.
-__device__ __forceinline__ bool metropolis(double Ta, double Tb, double Ua, double Ub,
-                                           uint64_t seed, int id_lo, int64_t attempt) {
-  const double d = __dmul_rn(__dsub_rn(__ddiv_rn(1.0, Ta), __ddiv_rn(1.0, Tb)), __dsub_rn(Ua, Ub));
+// Metropolis rule of the Implementation section for the pair (a before b in
+// ladder order), generalised to parameter sets (T, lam) whose Hamiltonians
+// are K + lam U_LJ: D = (lam_a/T_a - lam_b/T_b)(U_a/lam_a - U_b/lam_b) with U
+// the stored (scaled) potential energies; lam = 1 gives
+// D = (1/T_a - 1/T_b)(U_a - U_b).  Accept iff D >= 0 or r < exp(D), r the
+// uniform of the lower replica id for this attempt.
+__device__ __forceinline__ bool metropolis(double Ta, double Tb, double la, double lb, double Ua,
+                                           double Ub, uint64_t seed, int id_lo, int64_t attempt) {
+  const double d = __dmul_rn(__dsub_rn(__ddiv_rn(la, Ta), __ddiv_rn(lb, Tb)),
+                             __dsub_rn(__ddiv_rn(Ua, la), __ddiv_rn(Ub, lb)));
   if (d >= 0.0) return true;
   const Uni4 u = uniforms(seed, (uint64_t)id_lo, (uint64_t)attempt, kTagExch, 0ull);
   return u.u0 < exp(d);
+}
+
+// Partner position of ladder position q: pairs (q, q + d) for q - o in
+// [0, d) modulo 2d, o = p d (p the parity offset); -1 when unpaired.
+__device__ __forceinline__ int ladder_partner(int q, int R, int p, int d) {
+  const int o = p * d;
+  if (q < o) return -1;
+  if ((q - o) % (2 * d) < d) return q + d < R ? q + d : -1;
+  return q - d;
 }
 
 __device__ __forceinline__ int pair_offset(int mode, uint64_t seed, int64_t attempt) {
@@ -611,32 +625,27 @@ __device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsDev
   ok = __all_sync(0xffffffffu, ok);
   if (!ok) return false;
   __threadfence();
-  // ranks of the temperatures (positive: their bit patterns order like the values)
-  const long long* key = reinterpret_cast<const long long*>(S.T + base);
+  // ladder keys T/lam (positive: their bit patterns order like the values)
+  for (int m = lane; m < R; m += 32)
+    fr.key[base + m] = __ldcg(S.T + base + m) / __ldcg(S.lam + base + m);
+  __syncwarp();
+  const long long* key = reinterpret_cast<const long long*>(fr.key + base);
   for (int m = lane; m < R; m += 32) {
-    const long long t = __ldcg(key + m);
+    const long long t = key[m];
     int rank = 0;
     for (int b = 0; b < R; ++b) {
-      const long long u = __ldcg(key + b);
+      const long long u = key[b];
       rank += (u < t) || (u == t && b < m);
     }
     fr.order[base + rank] = m;
     fr.pos[base + m] = rank;
   }
   __syncwarp();
-  // pairs (q, q + 1) of the sorted order for q = p, p + 2, ...
   const int p = pair_offset(E.parity_mode, E.seed, attempt);
+  const int d = max(1, E.xdist);
   for (int m = lane; m < R; m += 32) {
-    const int q = fr.pos[base + m];
-    int partner = -1;
-    if (q >= p) {
-      if (((q - p) & 1) == 0) {
-        if (q + 1 < R) partner = fr.order[base + q + 1];
-      } else {
-        partner = fr.order[base + q - 1];
-      }
-    }
-    fr.partner[base + m] = partner;
+    const int q = ladder_partner(fr.pos[base + m], R, p, d);
+    fr.partner[base + m] = q < 0 ? -1 : fr.order[base + q];
   }
   __syncwarp();
   if (lane == 0) {
@@ -646,19 +655,25 @@ __device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsDev
   return true;
 }
 
-// A replica's part of pattern k (one thread).  Returns the velocity scale
-// sqrt(T_new / T_old) (1 when not accepted); *ok = false when the wait gave up.
+// A replica's part of pattern k (one thread), parameters (Tcur, lcur).
+// Returns the velocity scale sqrt(T_new / T_old) and sets *us =
+// lam_new / lam_old (both 1 when not accepted); *ok = false when the wait
+// gave up.
 __device__ double pair_exchange(const FreeDev& fr, const StateDev& S, const EnsDev& E,
                                 const RepDev& rd, int r, int k, int64_t attempt, double Tcur,
-                                double U, double* Tnew, int* partner_out, int* acc_out, bool* ok) {
+                                double lcur, double U, double* Tnew, double* lnew, double* us,
+                                int* partner_out, int* acc_out, bool* ok) {
   const int p = __ldcg(fr.partner + r);
   *Tnew = Tcur;
+  *lnew = lcur;
+  *us = 1.0;
   *partner_out = p;
   *acc_out = 0;
   *ok = true;
   if (p < 0) return 1.0;
-  fr.slot[2 * r] = Tcur;
-  fr.slot[2 * r + 1] = U;
+  fr.slot[3 * r] = Tcur;
+  fr.slot[3 * r + 1] = U;
+  fr.slot[3 * r + 2] = lcur;
   __threadfence();
   st_release(fr.flag + r, k + 1);
   const int gp = E.rep_off + p;
@@ -667,19 +682,22 @@ __device__ double pair_exchange(const FreeDev& fr, const StateDev& S, const EnsD
     return 1.0;
   }
   __threadfence();
-  const double Tp = __ldcg(fr.slot + 2 * gp), Up = __ldcg(fr.slot + 2 * gp + 1);
+  const double Tp = __ldcg(fr.slot + 3 * gp), Up = __ldcg(fr.slot + 3 * gp + 1),
+               lp = __ldcg(fr.slot + 3 * gp + 2);
   const int q = __ldcg(fr.pos + r), qp = __ldcg(fr.pos + gp);
-  const bool colder = q < qp;
+  const bool lower = q < qp;  // this replica comes first in ladder order
   const int id_lo = min(rd.id, p);
-  const bool accept = colder ? metropolis(Tcur, Tp, U, Up, E.seed, id_lo, attempt)
-                             : metropolis(Tp, Tcur, Up, U, E.seed, id_lo, attempt);
-  if (colder) {
+  const bool accept = lower ? metropolis(Tcur, Tp, lcur, lp, U, Up, E.seed, id_lo, attempt)
+                            : metropolis(Tp, Tcur, lp, lcur, Up, U, E.seed, id_lo, attempt);
+  if (lower) {
     atomicAdd(reinterpret_cast<unsigned long long*>(S.pair_att + E.pair_off + q), 1ull);
     if (accept) atomicAdd(reinterpret_cast<unsigned long long*>(S.pair_acc + E.pair_off + q), 1ull);
   }
   if (!accept) return 1.0;
   *acc_out = 1;
   *Tnew = Tp;
+  *lnew = lp;
+  *us = lp / lcur;
   return sqrt(Tp / Tcur);
 }
 
@@ -718,7 +736,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   // free-running exchange: the result handed to the cluster (velocity scale,
   // new T, status), the replica's current T and the launch's first attempt
   // number (thread 0), own steps since the last pattern (warp 0 of CTA 0)
-  __shared__ double xs_sh, xT_sh, Tcur_sh;
+  __shared__ double xs_sh, xT_sh, xl_sh, xu_sh, Tcur_sh;
   __shared__ long long A0_sh;
   __shared__ int xst_sh, since_sh, fold0_sh;
   cg::cluster_group cl = cg::this_cluster();
@@ -730,6 +748,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     E = ens[rd.ens];
     K = E.kc;
     set_thermo_target(K, S.T[r]);
+    set_potential_scale(K, S.lam[r]);
     Tcur_sh = S.T[r];
     A0_sh = S.attempt[rd.ens];
     since_sh = 0;
@@ -759,6 +778,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const int status0 = S.status[r];
   const int valid0 = S.valid[r];
   const double vs0 = S.vscale[r];
+  const double fs0 = S.fscale[r];
   double econs = S.econs[r];
   const int64_t step0 = S.step[r];
 
@@ -798,7 +818,6 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const uint32_t ncols = LSM ? (uint32_t)(per * P) : (uint32_t)(N * P);
   const uint32_t mycol = LSM ? (uint32_t)((i - i0) * P + q) : (uint32_t)(i * P + q);
   int32_t* ncnt = S.ncnt + (size_t)rd.atom_off * 8;
-  const float hl = (float)(K.hdt * K.lam32);  // FP32 half-kick factor per force unit
   const float dtqf = (float)K.dtq;
   const float ucf = (float)K.uc;
   const bool thermo = E.tau > 0.0;  // decided once; no FP64 tests inside the step loop
@@ -821,7 +840,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     if (own && d < 3) {
       xq[j] = qcomp(S, d)[g];
       const double vv = vcomp(S, d)[g] * vs0;
-      const double ff = fcomp(S, d)[g];
+      const double ff = fcomp(S, d)[g] * fs0;
       ref[j] = rcomp(S, d)[g];
       if (FP64) {
         v[j] = vv;
@@ -933,7 +952,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         for (int j = 0; j < ND; ++j) {
           const int d = q + j * P;
           if (d >= 3) continue;
-          f[j] = d == 0 ? fx : (d == 1 ? fy : fz);
+          f[j] = K.lamv * (d == 0 ? fx : (d == 1 ? fy : fz));
           if (kick) v[j] += K.hdt * f[j];
           dk += v[j] * v[j];
         }
@@ -962,7 +981,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         for (int j = 0; j < ND; ++j) {
           const int d = q + j * P;
           if (d >= 3) continue;
-          hf[j] = (d == 0 ? ax : (d == 1 ? ay : az)) * hl;
+          hf[j] = (d == 0 ? ax : (d == 1 ? ay : az)) * K.hlf;
           const float w = kick ? vf[j] + hf[j] : vf[j];
           kl = fmaf(w, w, kl);
         }
@@ -1041,13 +1060,13 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     if (FP64) {
       double su, sk;
       totals_fp64(su, sk, status);
-      U = 0.5 * su;
+      U = 0.5 * su * K.lamv;
       Kin = 0.5 * sk;
       if (!isfinite(U) || !isfinite(Kin)) status |= kStNumeric;
     } else {
       long long iu, ik;
       totals_int(iu, ik, status, true);
-      U = 0.5 * (double)iu * kEnUnit;  // FP64 only for the stored energies
+      U = 0.5 * (double)iu * kEnUnit * K.lamv;  // FP64 only for the stored energies
       Kin = 0.5 * (double)ik * kEnUnit;
     }
   }
@@ -1139,7 +1158,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       totals_fp64(su, sk, st);
       st &= ~(int)kStXchg;
       if (z.bad) st |= kStRngCap;
-      const double Un = 0.5 * su, Kn = 0.5 * sk;
+      const double Un = 0.5 * su * K.lamv, Kn = 0.5 * sk;
       // one lane forms the FP64 factor and K'; the CTA reads both after the
       // barrier, so every thread takes the same decisions below
       if (tid == 0) {
@@ -1215,7 +1234,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           econs += warp_sum(dsum);
           kp = __shfl_sync(0xffffffffu, kp, (slot - fold0) & 31);
           Kin = kp;
-          if (energy) U = 0.5 * (double)iu * kEnUnit;
+          if (energy) U = 0.5 * (double)iu * kEnUnit * K.lamv;
           __syncwarp();
           if (lane == 0) fold0_sh = slot + 1 == kNoiseChunk ? 0 : slot + 1;
           __syncwarp();
@@ -1233,11 +1252,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       // this replica's part of the pattern: CTA 0 runs the pair protocol and
       // hands the result to every CTA of the cluster
       if (crank == 0 && tid == 0) {
-        double Tn;
+        double Tn, ln, us;
         int pid, acc;
         bool ok;
-        const double sc = pair_exchange(fr, S, E, rd, r, k_next, A0_sh + k_next, Tcur_sh, U, &Tn,
-                                        &pid, &acc, &ok);
+        const double sc = pair_exchange(fr, S, E, rd, r, k_next, A0_sh + k_next, Tcur_sh, K.lamv,
+                                        U, &Tn, &ln, &us, &pid, &acc, &ok);
         if (k_next < fr.log_cap) {
           const size_t li = (size_t)k_next * fr.rtot + r;
           fr.log_step[li] = step0 + done;
@@ -1246,14 +1265,17 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           fr.log_acc[li] = acc;
         }
         if (Tn != Tcur_sh) S.T[r] = Tn;
+        if (ln != K.lamv) S.lam[r] = ln;
         for (int rk = 0; rk < C; ++rk) {
           *cl.map_shared_rank(&xs_sh, rk) = sc;
           *cl.map_shared_rank(&xT_sh, rk) = Tn;
+          *cl.map_shared_rank(&xl_sh, rk) = ln;
+          *cl.map_shared_rank(&xu_sh, rk) = us;
           *cl.map_shared_rank(&xst_sh, rk) = ok ? 0 : (int)kStTimeout;
         }
       }
       csync();  // B3
-      const double sc = xs_sh, Tn = xT_sh;
+      const double sc = xs_sh, Tn = xT_sh, ln = xl_sh, us = xu_sh;
       status |= xst_sh;
       if (tid == 0) atomicAnd(&sm.slot_st[0], ~(int)kStXchg);
       if (own && sc != 1.0) {
@@ -1269,14 +1291,30 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           }
         }
       }
+      if (own && us != 1.0) {
+        // the new Hamiltonian's forces: scale by lam_new / lam_old
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          if (FP64) f[j] *= us;
+          else hf[j] *= (float)us;
+        }
+      }
       const double Ks = Kin * (sc * sc);
       econs += Kin - Ks;
       Kin = Ks;
+      const double Us = U * us;
+      econs += U - Us;
+      U = Us;
+      // read by the other threads only after the next barriers; the lam
+      // comparison reads K before thread 0 may change it
+      const bool new_lam = ln != K.lamv;
+      __syncthreads();
       if (tid == 0) {
         if (Tn != Tcur_sh) {
-          set_thermo_target(K, Tn);  // read by others only after the next barriers
+          set_thermo_target(K, Tn);
           Tcur_sh = Tn;
         }
+        if (new_lam) set_potential_scale(K, ln);
         since_sh = 0;
       }
       if (crank == 0 && tid == 0) {
@@ -1328,6 +1366,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     S.step[r] = step0 + done;
     S.nreb[r] += nreb;
     S.vscale[r] = 1.0;
+    S.fscale[r] = 1.0;
     S.status[r] = status & ~(int)(kStStop | kStXchg);
     S.valid[r] = (status & kStOverflow) ? 0 : 1;
   }
@@ -1349,13 +1388,14 @@ __global__ void plain_kick_drift(StateDev S, const EnsDev* __restrict__ ens,
   const EnsDev E = ens[rd.ens];
   const StepConst& K = E.kc;
   const double vs = S.vscale[r];
+  const double fs = S.fscale ? S.fscale[r] : 1.0;  // pending force factor (exchange of lam)
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float md = 0.0f;
   if (i < E.N) {
     const int g = rd.atom_off + i;
-    const double vx = fma(S.vx[g], vs, K.hdt * S.fx[g]);
-    const double vy = fma(S.vy[g], vs, K.hdt * S.fy[g]);
-    const double vz = fma(S.vz[g], vs, K.hdt * S.fz[g]);
+    const double vx = fma(S.vx[g], vs, K.hdt * (S.fx[g] * fs));
+    const double vy = fma(S.vy[g], vs, K.hdt * (S.fy[g] * fs));
+    const double vz = fma(S.vz[g], vs, K.hdt * (S.fz[g] * fs));
     S.vx[g] = vx;
     S.vy[g] = vy;
     S.vz[g] = vz;
@@ -1455,12 +1495,16 @@ __global__ void plain_forces(StateDev S, const EnsDev* __restrict__ ens,
         e += 4.0 * (s3 * s3 - s3) - K.uc;
       }
     }
-    S.fx[g] = fx;
-    S.fy[g] = fy;
-    S.fz[g] = fz;
+    const double lam = S.lam ? S.lam[r] : 1.0;
+    S.fx[g] = lam * fx;
+    S.fy[g] = lam * fy;
+    S.fz[g] = lam * fz;
+    e *= lam;
   }
   e = block_sum(e, scr);
   if (threadIdx.x == 0) S.red[(size_t)r * kPlainRed + blockIdx.x] = e;
+  // the forces are new: no pending factor (plain_kick_drift of this step has run)
+  if (S.fscale && blockIdx.x == 0 && threadIdx.x == 0) S.fscale[r] = 1.0;
 }
 
 // Second half kick (optional) and per-block sums of v^2 to red[r][512 + block].
@@ -1545,35 +1589,43 @@ __device__ void rank_sort(const double* Ts, int* order, int R) {
   }
 }
 
+// One exchange attempt per ensemble (one CTA each): ladder keys T/lam sorted,
+// pairs (q, q + d) of the ladder (d = 1: sorted neighbours), the Metropolis
+// rule, and on acceptance the parameter sets (T, lam) are swapped: the
+// velocities take the pending factor sqrt(T_new/T_old), the forces
+// lam_new/lam_old, K and U follow and econs absorbs both changes.
 __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int32_t* partner_out,
                                 uint8_t* acc_out) {
   extern __shared__ __align__(16) unsigned char sh[];
   const EnsDev E = ens[blockIdx.x];
   const int R = E.R, base = E.rep_off;
-  double* Ts = reinterpret_cast<double*>(sh);
-  int* order = reinterpret_cast<int*>(Ts + R);
+  double* key = reinterpret_cast<double*>(sh);
+  int* order = reinterpret_cast<int*>(key + R);
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
-    Ts[a] = S.T[base + a];
+    key[a] = S.T[base + a] / S.lam[base + a];
     if (partner_out) partner_out[base + a] = -1;
     if (acc_out) acc_out[base + a] = 0;
   }
   __syncthreads();
-  rank_sort(Ts, order, R);
+  rank_sort(key, order, R);
   __syncthreads();
   const int64_t attempt = S.attempt[blockIdx.x];
   const int p = pair_offset(E.parity_mode, E.seed, attempt);
-  for (int k = p + 2 * threadIdx.x; k + 1 < R; k += 2 * blockDim.x) {
-    const int a = order[k], b = order[k + 1];
+  const int d = max(1, E.xdist);
+  for (int q = threadIdx.x; q < R; q += blockDim.x) {
+    const int qb = ladder_partner(q, R, p, d);
+    if (qb <= q) continue;  // unpaired, or the upper member of its pair
+    const int a = order[q], b = order[qb];
     const int ga = base + a, gb = base + b;
-    const double Ta = Ts[a], Tb = Ts[b];
-    const bool ok = metropolis(Ta, Tb, S.U[ga], S.U[gb], E.seed, min(a, b), attempt);
+    const double Ta = S.T[ga], Tb = S.T[gb], la = S.lam[ga], lb = S.lam[gb];
+    const bool ok = metropolis(Ta, Tb, la, lb, S.U[ga], S.U[gb], E.seed, min(a, b), attempt);
     if (partner_out) {
       partner_out[ga] = b;
       partner_out[gb] = a;
     }
-    S.pair_att[E.pair_off + k] += 1;
+    S.pair_att[E.pair_off + q] += 1;
     if (ok) {
-      S.pair_acc[E.pair_off + k] += 1;
+      S.pair_acc[E.pair_off + q] += 1;
       if (acc_out) acc_out[ga] = acc_out[gb] = 1;
       const double sa = sqrt(Tb / Ta), sb = sqrt(Ta / Tb);
       const double Ka = S.K[ga], Kb = S.K[gb];
@@ -1586,6 +1638,19 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
       S.K[gb] = Kbn;
       S.T[ga] = Tb;
       S.T[gb] = Ta;
+      if (la != lb) {
+        const double ua = lb / la, ub = la / lb;
+        const double Ua = S.U[ga], Ub = S.U[gb];
+        const double Uan = Ua * ua, Ubn = Ub * ub;
+        S.fscale[ga] *= ua;
+        S.fscale[gb] *= ub;
+        S.econs[ga] += Ua - Uan;
+        S.econs[gb] += Ub - Ubn;
+        S.U[ga] = Uan;
+        S.U[gb] = Ubn;
+        S.lam[ga] = lb;
+        S.lam[gb] = la;
+      }
     }
   }
   __syncthreads();
@@ -1593,27 +1658,36 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
 }
 
 __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
+                                    const double* __restrict__ lam,
                                     const double* __restrict__ U, uint64_t seed, int64_t attempt,
-                                    int mode, double* T_out, int32_t* partner, uint8_t* acc,
-                                    double* vscale) {
+                                    int mode, int distance, double* T_out, double* lam_out,
+                                    int32_t* partner, uint8_t* acc, double* vscale,
+                                    double* uscale) {
   extern __shared__ __align__(16) unsigned char sh[];
-  double* Ts = reinterpret_cast<double*>(sh);
-  int* order = reinterpret_cast<int*>(Ts + R);
+  double* key = reinterpret_cast<double*>(sh);
+  int* order = reinterpret_cast<int*>(key + R);
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
-    Ts[a] = T[a];
+    const double l = lam ? lam[a] : 1.0;
+    key[a] = T[a] / l;
     T_out[a] = T[a];
+    if (lam_out) lam_out[a] = l;
     partner[a] = -1;
     acc[a] = 0;
     vscale[a] = 1.0;
+    if (uscale) uscale[a] = 1.0;
   }
   __syncthreads();
-  rank_sort(Ts, order, R);
+  rank_sort(key, order, R);
   __syncthreads();
   const int p = pair_offset(mode, seed, attempt);
-  for (int k = p + 2 * threadIdx.x; k + 1 < R; k += 2 * blockDim.x) {
-    const int a = order[k], b = order[k + 1];
-    const double Ta = Ts[a], Tb = Ts[b];
-    const bool ok = metropolis(Ta, Tb, U[a], U[b], seed, min(a, b), attempt);
+  const int d = max(1, distance);
+  for (int q = threadIdx.x; q < R; q += blockDim.x) {
+    const int qb = ladder_partner(q, R, p, d);
+    if (qb <= q) continue;
+    const int a = order[q], b = order[qb];
+    const double Ta = T[a], Tb = T[b];
+    const double la = lam ? lam[a] : 1.0, lb = lam ? lam[b] : 1.0;
+    const bool ok = metropolis(Ta, Tb, la, lb, U[a], U[b], seed, min(a, b), attempt);
     partner[a] = b;
     partner[b] = a;
     if (ok) {
@@ -1622,6 +1696,14 @@ __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
       vscale[b] = sqrt(Ta / Tb);
       T_out[a] = Tb;
       T_out[b] = Ta;
+      if (lam_out) {
+        lam_out[a] = lb;
+        lam_out[b] = la;
+      }
+      if (uscale) {
+        uscale[a] = lb / la;
+        uscale[b] = la / lb;
+      }
     }
   }
 }
@@ -1633,18 +1715,26 @@ __global__ void apply_vscale_kernel(StateDev S, const RepDev* __restrict__ reps,
   const RepDev rd = reps[r];
   const int N = ens[rd.ens].N;
   const double vs = S.vscale[r];
-  if (vs == 1.0) return;
+  const double fs = S.fscale ? S.fscale[r] : 1.0;
+  if (vs == 1.0 && fs == 1.0) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int g = rd.atom_off + i;
     S.vx[g] *= vs;
     S.vy[g] *= vs;
     S.vz[g] *= vs;
+    S.fx[g] *= fs;
+    S.fy[g] *= fs;
+    S.fz[g] *= fs;
   }
 }
 
+// resets the pending velocity and force factors (after apply_vscale_kernel)
 __global__ void reset_vscale_kernel(StateDev S, int r0, int n_rep) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < n_rep) S.vscale[r0 + r] = 1.0;
+  if (r < n_rep) {
+    S.vscale[r0 + r] = 1.0;
+    if (S.fscale) S.fscale[r0 + r] = 1.0;
+  }
 }
 
 __global__ void export_kernel(StateDev S, const EnsDev* __restrict__ ens,
@@ -1701,6 +1791,7 @@ __global__ void import_kernel(StateDev S, const EnsDev* __restrict__ ens,
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S.valid[r] = 0;
     S.vscale[r] = 1.0;
+    if (S.fscale) S.fscale[r] = 1.0;
     S.status[r] = 0;
   }
 }
@@ -2001,14 +2092,20 @@ cudaError_t launch_spatial_sort(const StateDev& s, const EnsDev* d_ens, const Re
   return cudaGetLastError();
 }
 
-cudaError_t launch_exchange_raw(int R, const double* T, const double* U, uint64_t seed,
-                                int64_t attempt, int parity_mode, double* T_out,
-                                int32_t* partner, uint8_t* accepted, double* vscale,
+cudaError_t launch_exchange_raw(int R, const double* T, const double* lam, const double* U,
+                                uint64_t seed, int64_t attempt, int parity_mode, int distance,
+                                double* T_out, double* lam_out, int32_t* partner,
+                                uint8_t* accepted, double* vscale, double* uscale,
                                 cudaStream_t st) {
   const size_t smem = (size_t)R * (sizeof(double) + sizeof(int));
   const int threads = R >= 512 ? 512 : ((R + 31) / 32) * 32;
-  exchange_raw_kernel<<<1, threads, smem, st>>>(R, T, U, seed, attempt, parity_mode, T_out,
-                                                partner, accepted, vscale);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(exchange_raw_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  exchange_raw_kernel<<<1, threads, smem, st>>>(R, T, lam, U, seed, attempt, parity_mode, distance,
+                                               T_out, lam_out, partner, accepted, vscale, uscale);
   return cudaGetLastError();
 }
 
