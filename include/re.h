@@ -83,6 +83,10 @@ typedef struct re_opts {
                        neighbours).  Non-nearest exchanges are the extension the
                        Implementation section mentions: positions (q, q + d) in
                        blocks of 2d, offset by d on odd attempts (parity). */
+  int id_offset;    /* Philox stream of replica k's own draws (initial velocities,
+                       thermostat) is id_offset + k (default 0).  A ladder sharded
+                       over several contexts gives each shard the global id of its
+                       first member, so every replica keeps its own stream. */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -184,6 +188,15 @@ int re_energies(re_ctx *c, double *U, double *K, double *H);
 int re_temps(re_ctx *c, double *T);
 /* Potential scale lam of every replica id (host, n_rep values). */
 int re_lambdas(re_ctx *c, double *lam);
+
+/* Applies exchange results decided outside the context (a ladder sharded
+ * over several contexts or processes, each holding a block of its members):
+ * per replica id (host, n_rep values) the new T, the new lam (NULL: kept),
+ * the velocity factor sqrt(T_new/T_old) and the force/energy factor
+ * lam_new/lam_old (NULL: 1), with the same bookkeeping as re_exchange
+ * (K, U and econs).  All values must be positive.  Synchronous. */
+int re_apply_exchange(re_ctx *c, const double *T_new, const double *lam_new,
+                      const double *vscale, const double *uscale);
 /* Positions (wrapped into [0, L)) and velocities, host arrays of
  * 3 * (atoms of all replicas) doubles each; either may be NULL. */
 int re_get_state(re_ctx *c, double *x, double *v);

@@ -34,7 +34,7 @@ class _Opts(C.Structure):
                 ("shift_energy", C.c_int), ("precision", C.c_int), ("path", C.c_int),
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
                 ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int),
-                ("sort_interval", C.c_int), ("exch_distance", C.c_int)]
+                ("sort_interval", C.c_int), ("exch_distance", C.c_int), ("id_offset", C.c_int)]
 
 
 _lib = None
@@ -68,6 +68,7 @@ def lib():
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
         L.re_lambdas.argtypes = [vp, dp]
+        L.re_apply_exchange.argtypes = [vp, dp, dp, dp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
         L.re_set_state.argtypes = [vp, dp, dp]
         L.re_forces.argtypes = [vp, dp]
@@ -118,7 +119,7 @@ class Context:
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
                  cell_div=0, cluster=0, atom_threads=0, sort_interval=0, lam=None,
-                 exch_distance=1, _handle=None):
+                 exch_distance=1, id_offset=0, _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -132,6 +133,7 @@ class Context:
             o.cell_div, o.cluster, o.atom_threads = cell_div, cluster, atom_threads
             o.sort_interval = sort_interval
             o.exch_distance = exch_distance
+            o.id_offset = id_offset
             t = np.ascontiguousarray(temps, dtype=np.float64)
             lp = None
             if lam is not None:
@@ -232,6 +234,14 @@ class Context:
         T = np.zeros(self.n_rep)
         _check(lib().re_temps(self._h, _p(T, C.c_double)), self._h)
         return T
+
+    def apply_exchange(self, T_new, vscale, lam_new=None, uscale=None):
+        """Applies exchange results decided elsewhere (host arrays, n_rep)."""
+        f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        T_new, vscale, lam_new, uscale = f(T_new), f(vscale), f(lam_new), f(uscale)
+        q = lambda a: None if a is None else _p(a, C.c_double)
+        _check(lib().re_apply_exchange(self._h, q(T_new), q(lam_new), q(vscale), q(uscale)),
+               self._h)
 
     def lambdas(self):
         lam = np.zeros(self.n_rep)

@@ -471,6 +471,7 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
       RepDev rd{};
       rd.ens = (int)k;
       rd.id = r;
+      rd.stream = c->opt.id_offset + r;
       rd.atom_off = (int)atom_off;
       rd.nbr_off = nbr_off;
       c->reps.push_back(rd);
@@ -522,6 +523,7 @@ void re_default_opts(re_opts* o) {
   o->atom_threads = 0;
   o->sort_interval = 0;
   o->exch_distance = 1;
+  o->id_offset = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -555,6 +557,7 @@ int re_create_h(int N, double L, double rc, int n_rep, const double* temps, cons
   if (o.path == RE_PATH_PLAIN) o.precision = RE_PREC_FP64;
   if (o.nx < 0) return fail(nullptr, RE_EINVAL, "nx must be >= 0");
   if (o.exch_distance < 0) return fail(nullptr, RE_EINVAL, "exch_distance must be >= 1");
+  if (o.id_offset < 0) return fail(nullptr, RE_EINVAL, "id_offset must be >= 0");
   for (int i = 0; i < n_rep; ++i) {
     if (!(temps[i] > 0) || !std::isfinite(temps[i]))
       return fail(nullptr, RE_EINVAL, "temperatures must be positive");
@@ -966,6 +969,31 @@ int re_energies(re_ctx* c, double* U, double* K, double* H) {
     if (K) K[r] = k[r];
     if (H) H[r] = u[r] + k[r] + e[r];
   }
+  return RE_OK;
+}
+
+int re_apply_exchange(re_ctx* c, const double* T_new, const double* lam_new,
+                      const double* vscale, const double* uscale) {
+  if (!c || !T_new || !vscale) return fail(c, RE_EINVAL, "bad arguments");
+  const int R = c->n_rep;
+  std::vector<double> in(4 * (size_t)R);
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (!lam_new)
+    RE_CUDA(c, cudaMemcpy(in.data() + R, c->s.lam, 8 * (size_t)R, cudaMemcpyDeviceToHost),
+            "read lam");
+  for (int r = 0; r < R; ++r) {
+    in[r] = T_new[r];
+    if (lam_new) in[R + r] = lam_new[r];
+    in[2 * R + r] = vscale[r];
+    in[3 * R + r] = uscale ? uscale[r] : 1.0;
+    if (!(in[r] > 0) || !(in[R + r] > 0) || !(in[2 * R + r] > 0) || !(in[3 * R + r] > 0))
+      return fail(c, RE_EINVAL, "replica %d: T, lam and the factors must be positive", r);
+  }
+  RE_CUDA(c, cudaMemcpyAsync(c->d_io, in.data(), 8 * in.size(), cudaMemcpyHostToDevice,
+                             c->stream), "upload exchange");
+  cudaError_t e = re::launch_apply_exchange(c->s, c->d_io, R, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "apply exchange");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
   return RE_OK;
 }
 

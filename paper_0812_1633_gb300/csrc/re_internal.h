@@ -73,7 +73,8 @@ __host__ __device__ inline void set_thermo_target(StepConst& k, double T) {
 }
 
 struct RepDev {
-  int ens, id, atom_off, pad_;
+  int ens, id, atom_off;
+  int stream;  // Philox stream of the replica's own draws (velocities, thermostat): id_offset + id
   int64_t nbr_off;
 };
 
@@ -158,6 +159,9 @@ cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev*
 // Clusters of the batched kernel that can be resident at once with this
 // launch shape (0 when the query fails).
 int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int max_ncell);
+// applies externally decided exchange results, d_in = [T_new | lam_new |
+// vscale | uscale] (R values each, device)
+cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, cudaStream_t st);
 // attempt[e] += n for every ensemble (after a free-running launch)
 cudaError_t launch_attempt_add(const StateDev& s, int n_ens, int n, cudaStream_t st);
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,

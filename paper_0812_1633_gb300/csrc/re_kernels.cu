@@ -63,7 +63,7 @@ __global__ void init_lattice_kernel(StateDev S, const EnsDev* __restrict__ ens,
     S.qx[g] = fix_from_double(x, inv_l);
     S.qy[g] = fix_from_double(y, inv_l);
     S.qz[g] = fix_from_double(z, inv_l);
-    const Uni4 u = uniforms(E.seed, (uint64_t)rd.id, (uint64_t)i, kTagVel, 0ull);
+    const Uni4 u = uniforms(E.seed, (uint64_t)rd.stream, (uint64_t)i, kTagVel, 0ull);
     double g0, g1, g2, g3;
     box_muller(u.u0, u.u1, &g0, &g1);
     box_muller(u.u2, u.u3, &g2, &g3);
@@ -1080,7 +1080,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     SvrStep* sv = reinterpret_cast<SvrStep*>(sm.noise) + ((s / kNoiseChunk) & 1) * kNoiseChunk;
     if (thermo && (s % kNoiseChunk) == 0 && tid < kNoiseChunk && s + tid < B) {
       int capped = 0;
-      SvrStep z = svr_step(FP64, K, E.seed, (uint64_t)rd.id, (uint64_t)(n + tid), &capped);
+      SvrStep z = svr_step(FP64, K, E.seed, (uint64_t)rd.stream, (uint64_t)(n + tid), &capped);
       z.bad = capped;
       sv[tid] = z;
     }
@@ -1554,7 +1554,7 @@ __global__ void plain_thermo(StateDev S, const EnsDev* __restrict__ ens,
     if (thermo && E.tau > 0.0) {
       const int nf = 3 * E.N - 3;
       int capped = 0;
-      const double2 nz = svr_noise(nf, E.seed, (uint64_t)rd.id, (uint64_t)S.step[r], &capped);
+      const double2 nz = svr_noise(nf, E.seed, (uint64_t)rd.stream, (uint64_t)S.step[r], &capped);
       if (capped) st |= kStRngCap;
       alpha = svr_alpha(Kn, 0.5 * nf * S.T[r], nf, exp(-E.dt / E.tau), nz.x, nz.y, &Kp);
       S.econs[r] += Kn - Kp;
@@ -1706,6 +1706,29 @@ __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
       }
     }
   }
+}
+
+// Exchange results decided elsewhere (a ladder sharded over several
+// contexts): in = [T_new | lam_new | vscale | uscale], R values each.  The same
+// bookkeeping as exchange_kernel for an accepted pair.
+__global__ void apply_exchange_kernel(StateDev S, const double* __restrict__ in, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const double vs = in[2 * R + r], us = in[3 * R + r];
+  if (vs != 1.0) {
+    const double K = S.K[r], Kn = K * (vs * vs);
+    S.econs[r] += K - Kn;
+    S.K[r] = Kn;
+    S.vscale[r] *= vs;
+  }
+  if (us != 1.0) {
+    const double U = S.U[r], Un = U * us;
+    S.econs[r] += U - Un;
+    S.U[r] = Un;
+    S.fscale[r] *= us;
+  }
+  S.T[r] = in[r];
+  S.lam[r] = in[R + r];
 }
 
 // ------------------------------------------------------------------ state I/O
@@ -2033,6 +2056,11 @@ cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDe
     apply_vscale_kernel<<<dim3((N + 255) / 256, 1), 256, 0, st>>>(s, d_rep, d_ens, r);
     reset_vscale_kernel<<<1, 32, 0, st>>>(s, r, 1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, cudaStream_t st) {
+  apply_exchange_kernel<<<(R + 127) / 128, 128, 0, st>>>(s, d_in, R);
   return cudaGetLastError();
 }
 

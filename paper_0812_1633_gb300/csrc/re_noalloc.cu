@@ -106,6 +106,7 @@ extern "C" int re_lj_forces_device_noalloc(int N, double L, double rc, int shift
   re::RepDev rd{};
   rd.ens = 0;
   rd.id = 0;
+  rd.stream = 0;
   rd.atom_off = 0;
   rd.nbr_off = 0;
 
