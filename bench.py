@@ -404,7 +404,7 @@ def run_gpu(args, cfg):
         line = {
             "metric": "replica·atom-steps/s", "value": value, "unit": "replica·atom-steps/s",
             "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": 1e3 * total_s / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic (FCC start at rho 0.8442, seeded Philox velocities and budgets)",
             "config": {"workload": desc, "path": f"{prec} batched (one persistent launch per cycle)",
                        "l2": "flushed between timed steps (256 MB write)",

@@ -1078,11 +1078,18 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   for (int s = 0; s < B && status == 0 && !(freerun && k_next >= fr.n_att); ++s) {
     const int64_t n = step0 + s;
     SvrStep* sv = reinterpret_cast<SvrStep*>(sm.noise) + ((s / kNoiseChunk) & 1) * kNoiseChunk;
-    if (thermo && (s % kNoiseChunk) == 0 && tid < kNoiseChunk && s + tid < B) {
-      int capped = 0;
-      SvrStep z = svr_step(FP64, K, E.seed, (uint64_t)rd.stream, (uint64_t)(n + tid), &capped);
-      z.bad = capped;
-      sv[tid] = z;
+    // The thermostat records of the next kNoiseChunk steps.  Every CTA of the
+    // cluster makes its own identical copy and every record a step may read
+    // is written whatever the block size: the CTAs of a replica must take the
+    // same decisions (a CTA that left the step loop early would leave its
+    // partners writing into the shared memory of an exited block).
+    if (thermo && (s % kNoiseChunk) == 0) {
+      for (int t = tid; t < kNoiseChunk && s + t < B; t += T) {
+        int capped = 0;
+        SvrStep z = svr_step(FP64, K, E.seed, (uint64_t)rd.stream, (uint64_t)(n + t), &capped);
+        z.bad = capped;
+        sv[t] = z;
+      }
     }
     // (first half kick of the launch) + drift + displacement since the last rebuild
     float d2 = 0.0f;

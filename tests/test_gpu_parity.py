@@ -245,3 +245,30 @@ def test_non_finite_energy_is_reported(re):
     with pytest.raises(re.REError) as e:
         ctx.set_state(x, v)
     assert e.value.code == re.RE_ENUMERIC
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_small_blocks_match_oracle(re, prec):
+    """32 atoms and 32 threads per CTA (clusters of 8): fewer threads than
+    thermostat records per chunk; every CTA of a replica must still hold the
+    same records (budgets run past record 32 of the first chunk)."""
+    N, seed = 256, 3
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.4, 3)
+    ctx = re.Context(N, L, 2.5, temps, seed, precision=prec, cluster=8, atom_threads=1)
+    assert ctx.config()["threads"] == 32
+    ens = O.Ensemble(N, L, temps, seed)
+    budgets = [70, 40, 65]
+    ctx.advance(budgets)
+    ens.advance(budgets)
+    x, v = ctx.get_state()
+    U, K, H = ctx.energies()
+    steps, _ = ctx.counters()
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    for k, r in enumerate(ens.reps):
+        assert steps[k] == budgets[k]
+        d = x[k * N:(k + 1) * N] - r.x
+        d -= L * np.rint(d / L)
+        assert np.abs(d).max() < (tol if prec == "fp64" else 1e-4)
+        assert abs(U[k] - r.U) / N < (1e-12 if prec == "fp64" else 1e-5)
+        assert abs(K[k] - r.K) / N < (1e-12 if prec == "fp64" else 1e-5)
