@@ -87,6 +87,11 @@ typedef struct re_opts {
                        thermostat) is id_offset + k (default 0).  A ladder sharded
                        over several contexts gives each shard the global id of its
                        first member, so every replica keeps its own stream. */
+  int lists_smem;   /* neighbour lists of the batched path: 0 (default) global memory
+                       (cached in L1/L2); 1: each CTA's sub-lists in shared memory when
+                       they fit (copied in and out at every launch, so they pay off only
+                       for long launches); -1: global memory, also for re_autotune.
+                       re_autotune tries both unless this is 1 or -1. */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -217,6 +222,9 @@ int re_info(const re_ctx *c, int *n_rep, int64_t *n_atoms, int *n_ens, int *n_pa
 /* Launch configuration in use: CTAs per replica, threads per CTA, list cells
  * per list radius, threads per atom (any may be NULL). */
 int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads);
+/* re_config and whether the neighbour lists are kept in shared memory. */
+int re_config_ex(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads,
+                 int *lists_smem);
 /* Times candidate launch configurations (cluster, atom_threads, cell_div) over
  * `steps` steps each on a copy of the state and keeps the fastest; the state
  * is restored afterwards. */

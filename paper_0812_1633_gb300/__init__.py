@@ -34,7 +34,8 @@ class _Opts(C.Structure):
                 ("shift_energy", C.c_int), ("precision", C.c_int), ("path", C.c_int),
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
                 ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int),
-                ("sort_interval", C.c_int), ("exch_distance", C.c_int), ("id_offset", C.c_int)]
+                ("sort_interval", C.c_int), ("exch_distance", C.c_int), ("id_offset", C.c_int),
+                ("lists_smem", C.c_int)]
 
 
 _lib = None
@@ -68,6 +69,7 @@ def lib():
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
         L.re_lambdas.argtypes = [vp, dp]
+        L.re_config_ex.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
         L.re_apply_exchange.argtypes = [vp, dp, dp, dp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
         L.re_set_state.argtypes = [vp, dp, dp]
@@ -119,7 +121,7 @@ class Context:
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
                  cell_div=0, cluster=0, atom_threads=0, sort_interval=0, lam=None,
-                 exch_distance=1, id_offset=0, _handle=None):
+                 exch_distance=1, id_offset=0, lists_smem=0, _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -134,6 +136,7 @@ class Context:
             o.sort_interval = sort_interval
             o.exch_distance = exch_distance
             o.id_offset = id_offset
+            o.lists_smem = lists_smem
             t = np.ascontiguousarray(temps, dtype=np.float64)
             lp = None
             if lam is not None:
@@ -282,10 +285,11 @@ class Context:
         return a[:self.n_pairs], b[:self.n_pairs]
 
     def config(self):
-        cl, th, cd, at = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        lib().re_config(self._h, C.byref(cl), C.byref(th), C.byref(cd), C.byref(at))
+        cl, th, cd, at, ls = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        lib().re_config_ex(self._h, C.byref(cl), C.byref(th), C.byref(cd), C.byref(at),
+                           C.byref(ls))
         return {"cluster": cl.value, "threads": th.value, "cell_div": cd.value,
-                "atom_threads": at.value}
+                "atom_threads": at.value, "lists_smem": ls.value}
 
     def autotune(self, steps=10):
         _check(lib().re_autotune(self._h, int(steps)), self._h)

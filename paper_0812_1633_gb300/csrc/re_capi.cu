@@ -92,7 +92,7 @@ struct re_ctx {
   int n_rep = 0, n_pairs = 0;
   int64_t n_atoms = 0, n_nbr = 0;
   int max_n = 0, max_r = 0, max_ncell = 0;
-  LaunchCfg cfg{1, 256, 0, 1};
+  LaunchCfg cfg{1, 256, 0, 1, 0};
   cudaStream_t stream = nullptr;
   int device = 0;
   StateDev s{};
@@ -251,6 +251,7 @@ LaunchCfg default_cfg(const re_ctx* c) {
   k.atom_threads = p;
   k.threads = threads_for(c->max_n, cl, p);
   k.cell_div = 0;
+  k.lists_smem = c->opt.lists_smem > 0 ? 1 : 0;
   return k;
 }
 
@@ -343,6 +344,7 @@ int max_smem_optin() {
 // P sub-lists over all ensembles, or 0 when they would not fit (the kernel then
 // reads the lists from global memory).
 size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
+  if (!k.lists_smem) return 0;
   const int pidx = k.atom_threads == 1 ? 0 : (k.atom_threads == 2 ? 1 : (k.atom_threads == 4 ? 2 : 3));
   size_t elems = 0;
   for (const auto& e : c->ens) {
@@ -524,6 +526,7 @@ void re_default_opts(re_opts* o) {
   o->sort_interval = 0;
   o->exch_distance = 1;
   o->id_offset = 0;
+  o->lists_smem = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -1104,6 +1107,13 @@ int re_info(const re_ctx* c, int* n_rep, int64_t* n_atoms, int* n_ens, int* n_pa
   return RE_OK;
 }
 
+int re_config_ex(const re_ctx* c, int* cluster, int* threads, int* cell_div, int* atom_threads,
+                 int* lists_smem) {
+  if (!c) return RE_EINVAL;
+  if (lists_smem) *lists_smem = list_elems_for(c, c->cfg) > 0 ? 1 : 0;
+  return re_config(c, cluster, threads, cell_div, atom_threads);
+}
+
 int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div, int* atom_threads) {
   if (!c) return RE_EINVAL;
   if (cluster) *cluster = c->cfg.cluster;
@@ -1146,6 +1156,13 @@ int re_autotune(re_ctx* c, int steps) {
   std::vector<int32_t> bud(R, steps);
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget, bud.data(), 4 * R, cudaMemcpyHostToDevice, c->stream),
           "upload");
+  // budgets of one step for the untimed list build of every trial
+  int32_t* d_one = nullptr;
+  {
+    const std::vector<int32_t> ones(R, 1);
+    RE_CUDA(c, cudaMalloc(&d_one, 4 * R), "autotune budgets");
+    RE_CUDA(c, cudaMemcpy(d_one, ones.data(), 4 * R, cudaMemcpyHostToDevice), "autotune budgets");
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1168,18 +1185,25 @@ int re_autotune(re_ctx* c, int steps) {
     upload_tables(c);
     for (int ci = 0; ci < 4; ++ci) {
       if (c->opt.cluster > 0 && clusters[ci] != c->opt.cluster) continue;
-      for (int pi = 0; pi < 4; ++pi) {
-        if (c->opt.atom_threads > 0 && pvals[pi] != c->opt.atom_threads) continue;
-        LaunchCfg k{clusters[ci], threads_for(c->max_n, clusters[ci], pvals[pi]), m, pvals[pi]};
+      for (int pi = 0; pi < 8; ++pi) {
+        // lists in global memory, then in shared memory (when they fit)
+        const int ls = pi & 1;
+        if (c->opt.atom_threads > 0 && pvals[pi / 2] != c->opt.atom_threads) continue;
+        if ((c->opt.lists_smem > 0 && ls == 0) || (c->opt.lists_smem < 0 && ls == 1)) continue;
+        LaunchCfg k{clusters[ci], threads_for(c->max_n, clusters[ci], pvals[pi / 2]), m,
+                    pvals[pi / 2], ls};
         if ((c->max_n + k.cluster - 1) / k.cluster < 16) continue;
         if (check_cfg(c, k) != RE_OK) continue;
+        if (ls == 1 && list_elems_for(c, k) == 0) continue;
         c->cfg = k;
         float ms = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
-          // restore, force a rebuild so every trial starts alike, then time
+          // restore, force a rebuild so every trial starts alike (one step
+          // builds this shape's lists), then time a launch with valid lists
           for (auto& b : bufs)
             cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
           cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
+          if (launch_advance(c, d_one, nullptr, 1) != RE_OK) break;
           cudaEventRecord(e0, c->stream);
           if (launch_advance(c, c->d_budget, nullptr) != RE_OK) break;
           cudaEventRecord(e1, c->stream);
@@ -1216,6 +1240,7 @@ int re_autotune(re_ctx* c, int steps) {
   cudaStreamSynchronize(c->stream);
   c->tuning = false;
   for (auto& b : bufs) cudaFree(b.save);
+  cudaFree(d_one);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (c->graph) {

@@ -132,6 +132,7 @@ struct FreeDev {
 struct LaunchCfg {
   int cluster, threads, cell_div, atom_threads;  // CTAs per replica, threads per CTA,
                                                  // list cells per list radius, threads per atom
+  int lists_smem;  // 1: each CTA's sub-lists in shared memory during a launch (when they fit)
 };
 
 // Host helpers (re_capi.cu): list cells of an ensemble and neighbour capacities.

@@ -272,3 +272,23 @@ def test_small_blocks_match_oracle(re, prec):
         assert np.abs(d).max() < (tol if prec == "fp64" else 1e-4)
         assert abs(U[k] - r.U) / N < (1e-12 if prec == "fp64" else 1e-5)
         assert abs(K[k] - r.K) / N < (1e-12 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lists_in_shared_memory_equal_global(re, prec):
+    """Where the neighbour lists live (global memory, or copied into shared
+    memory at every launch) must not change a single bit."""
+    N = 500
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, 4)
+    a = re.Context(N, L, 2.5, temps, 17, precision=prec, lists_smem=0)
+    b = re.Context(N, L, 2.5, temps, 17, precision=prec, lists_smem=1)
+    assert a.config()["lists_smem"] == 0 and b.config()["lists_smem"] == 1
+    for c in range(6):
+        for ctx in (a, b):
+            ctx.advance(15)
+            ctx.exchange()
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.energies()[2], b.energies()[2])
