@@ -651,8 +651,8 @@ def run_diffusion(args):
 # capture per workload and launch shape (profiles/md_batched_kernel_64x864.md),
 # valid only while the kernel's sources are the ones that were profiled.
 PROFILED_TRAFFIC = {
-    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "2de82d11dfe9c239",
-                                 "bytes_per_launch": 23832064 + 23808},
+    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "bd1533beafd5c35e",
+                                 "bytes_per_launch": 14035968 + 5120},
 }
 
 
