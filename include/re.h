@@ -30,10 +30,11 @@
  *
  * Random numbers: Philox4x64-10 (Salmon et al., SC'11) used as a
  * counter-based generator; key = (seed, stream), counter = (index, tag, sub, 0):
- *   tag 1 initial velocities  (stream = replica id, index = atom)
- *   tag 2 thermostat Gaussian (stream = replica id, index = step)
- *   tag 3 thermostat Gamma trials (stream = replica id, index = step, sub = trial)
- *   tag 4 Metropolis uniform  (stream = replica id, index = attempt)
+ *   tag 1 initial velocities  (stream = id_offset + replica id, index = atom)
+ *   tag 2 thermostat Gaussian (stream = id_offset + replica id, index = step)
+ *   tag 3 thermostat Gamma trials (stream = id_offset + replica id, index = step,
+ *                                  sub = trial)
+ *   tag 4 Metropolis uniform  (stream = member id in the ladder, index = attempt)
  *   tag 5 random pair offset  (stream = 2^64-1, index = attempt)
  * A uniform is (word >> 11) * 2^-53.
  */
@@ -55,7 +56,9 @@ extern "C" {
 #define RE_ETIMEOUT (-6)  /* a bounded device wait gave up                    */
 
 #define RE_PREC_FP64 0    /* FP64 pair forces                                 */
-#define RE_PREC_MIXED 1   /* FP32 pair forces, FP64 accumulation and state    */
+#define RE_PREC_MIXED 1   /* FP32 pair forces on exact fixed-point separations,
+                             64-bit fixed-point positions and velocities, exact
+                             integer energy sums                               */
 
 #define RE_PATH_BATCHED 0 /* one persistent launch runs every replica's budget */
 #define RE_PATH_PLAIN 1   /* per replica and per step a sequence of launches  */
@@ -151,14 +154,14 @@ int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
  * (Implementation section): replicas integrate without stopping; in every
  * ensemble the master of attempt a (member a mod R, rotating) waits, after nx
  * of its own steps since it took part in attempt a - 1, until every member has
- * finished attempt a - 1, sorts the members' temperatures and publishes the
- * pattern (adjacent pairs in temperature order, offset by parity as in
- * re_exchange).  Every replica looks for a new pattern after each of its
- * steps; a paired replica publishes (T, U), waits for its partner's, and both
- * apply the Metropolis rule with the uniform of the lower replica id for
- * attempt a; on acceptance T is swapped and velocities scale by
- * sqrt(T_new/T_old), exactly as re_exchange does.  n_att attempts per
- * ensemble, then the launch ends.
+ * finished attempt a - 1, sorts the ladder and publishes the pattern (the
+ * pairs of re_exchange: ladder distance opt.exch_distance, offset by parity).
+ * Every replica looks for a new pattern after each of its steps; a paired
+ * replica publishes (T, U, lam), waits for its partner's, and both apply the
+ * Metropolis rule with the uniform of the lower replica id for attempt a; on
+ * acceptance the parameters are swapped and velocities (and forces) rescaled
+ * exactly as re_exchange does.  n_att attempts per ensemble, then the launch
+ * ends.
  *
  * Requires the batched path and all replicas resident on the GPU at once
  * (RE_EINVAL otherwise).  Every device wait is bounded (about 1 s); a wait
@@ -174,11 +177,12 @@ int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
 int re_run_free(re_ctx *c, int n_att, int nx, int64_t *log_step, double *log_T,
                 int32_t *log_partner, uint8_t *log_acc);
 
-/* One exchange attempt in every ensemble: temperatures sorted, sorted
- * neighbours paired from offset 0 or 1, Metropolis with the lower replica
- * id's uniform, accepted pairs swap T and rescale velocities.  Outputs (host,
- * n_rep each, may be NULL): partner id or -1, accepted flag.  Synchronises
- * only when an output is requested. */
+/* One exchange attempt in every ensemble: the ladder sorted (by temperature;
+ * by T/lam with potential scales), ladder positions (q, q + d) paired for
+ * d = opt.exch_distance (1: neighbours) from offset 0 or d, Metropolis with
+ * the lower replica id's uniform, accepted pairs swap T (and lam) and rescale
+ * velocities (and forces).  Outputs (host, n_rep each, may be NULL): partner
+ * id or -1, accepted flag.  Synchronises only when an output is requested. */
 int re_exchange(re_ctx *c, int32_t *partner_out, uint8_t *accepted_out);
 
 /* n_cycles times { re_advance(steps + cycle * n_rep); re_exchange }.  steps:
