@@ -104,6 +104,9 @@ struct re_ctx {
   int32_t* d_budget_run = nullptr;  // n_cycles * n_rep for re_run
   size_t budget_run_cap = 0;
   int32_t* h_ring = nullptr;        // pinned, kRing * n_rep
+  // pinned: per-replica results read back in one synchronisation
+  // (U, K, econs: doubles; status, partner: int32; accepted: bytes)
+  unsigned char* h_out = nullptr;
   cudaEvent_t ring_ev[kRing] = {};
   int ring_pos = 0;
   int32_t* d_partner = nullptr;
@@ -302,6 +305,7 @@ int allocate(re_ctx* c) {
     RE_CUDA(c, cudaMemcpy(s.fscale, ones.data(), 8 * R, cudaMemcpyHostToDevice), "init fscale");
   }
   RE_CUDA(c, cudaMallocHost(&c->h_ring, sizeof(int32_t) * R * kRing), "cudaMallocHost");
+  RE_CUDA(c, cudaMallocHost(&c->h_out, (3 * 8 + 2 * 4 + 1) * R), "cudaMallocHost");
   for (int k = 0; k < kRing; ++k)
     RE_CUDA(c, cudaEventCreateWithFlags(&c->ring_ev[k], cudaEventDisableTiming), "event");
   // work list: replicas by decreasing size (largest clusters start first)
@@ -423,11 +427,16 @@ int refresh(re_ctx* c) {
   return launch_advance(c, nullptr, zero.data());
 }
 
-int status_check(re_ctx* c) {
-  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
-  std::vector<int32_t> st(c->n_rep);
-  RE_CUDA(c, cudaMemcpy(st.data(), c->s.status, sizeof(int32_t) * c->n_rep,
-                        cudaMemcpyDeviceToHost), "read status");
+// Pinned read-back areas of h_out.
+double* out_U(re_ctx* c) { return reinterpret_cast<double*>(c->h_out); }
+double* out_K(re_ctx* c) { return out_U(c) + c->n_rep; }
+double* out_econs(re_ctx* c) { return out_U(c) + 2 * (size_t)c->n_rep; }
+int32_t* out_status(re_ctx* c) { return reinterpret_cast<int32_t*>(out_U(c) + 3 * (size_t)c->n_rep); }
+int32_t* out_partner(re_ctx* c) { return out_status(c) + c->n_rep; }
+uint8_t* out_acc(re_ctx* c) { return reinterpret_cast<uint8_t*>(out_partner(c) + c->n_rep); }
+
+// The first error recorded in the replicas' status words.
+int status_eval(re_ctx* c, const int32_t* st) {
   for (int r = 0; r < c->n_rep; ++r) {
     if (st[r] & re::kStOverflow)
       return fail(c, RE_EOVERFLOW, "replica %d: neighbour list capacity exceeded (%d per atom; "
@@ -440,6 +449,13 @@ int status_check(re_ctx* c) {
     if (st[r] & re::kStTimeout)
       return fail(c, RE_ETIMEOUT, "replica %d: free-running exchange wait gave up", r);
   return RE_OK;
+}
+
+int status_check(re_ctx* c) {
+  RE_CUDA(c, cudaMemcpyAsync(out_status(c), c->s.status, sizeof(int32_t) * c->n_rep,
+                             cudaMemcpyDeviceToHost, c->stream), "read status");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  return status_eval(c, out_status(c));
 }
 
 int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<re_ctx*>* src) {
@@ -857,13 +873,17 @@ int re_exchange(re_ctx* c, int32_t* partner_out, uint8_t* accepted_out) {
   cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r, c->d_partner,
                                       c->d_acc, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+  if (!partner_out && !accepted_out) return RE_OK;
+  // through the pinned read-back area: truly asynchronous copies, one wait
   if (partner_out)
-    RE_CUDA(c, cudaMemcpyAsync(partner_out, c->d_partner, sizeof(int32_t) * c->n_rep,
+    RE_CUDA(c, cudaMemcpyAsync(out_partner(c), c->d_partner, sizeof(int32_t) * c->n_rep,
                                cudaMemcpyDeviceToHost, c->stream), "read partners");
   if (accepted_out)
-    RE_CUDA(c, cudaMemcpyAsync(accepted_out, c->d_acc, c->n_rep, cudaMemcpyDeviceToHost,
-                               c->stream), "read accepted");
-  if (partner_out || accepted_out) RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+    RE_CUDA(c, cudaMemcpyAsync(out_acc(c), c->d_acc, c->n_rep, cudaMemcpyDeviceToHost, c->stream),
+            "read accepted");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (partner_out) std::memcpy(partner_out, out_partner(c), sizeof(int32_t) * c->n_rep);
+  if (accepted_out) std::memcpy(accepted_out, out_acc(c), c->n_rep);
   return RE_OK;
 }
 
@@ -960,13 +980,18 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
 
 int re_energies(re_ctx* c, double* U, double* K, double* H) {
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
-  int rc = status_check(c);
-  if (rc) return rc;
+  // status and energies in one synchronisation (pinned destinations)
   const size_t R = (size_t)c->n_rep;
-  std::vector<double> u(R), k(R), e(R);
-  RE_CUDA(c, cudaMemcpy(u.data(), c->s.U, 8 * R, cudaMemcpyDeviceToHost), "read U");
-  RE_CUDA(c, cudaMemcpy(k.data(), c->s.K, 8 * R, cudaMemcpyDeviceToHost), "read K");
-  RE_CUDA(c, cudaMemcpy(e.data(), c->s.econs, 8 * R, cudaMemcpyDeviceToHost), "read econs");
+  RE_CUDA(c, cudaMemcpyAsync(out_status(c), c->s.status, 4 * R, cudaMemcpyDeviceToHost, c->stream),
+          "read status");
+  RE_CUDA(c, cudaMemcpyAsync(out_U(c), c->s.U, 8 * R, cudaMemcpyDeviceToHost, c->stream), "read U");
+  RE_CUDA(c, cudaMemcpyAsync(out_K(c), c->s.K, 8 * R, cudaMemcpyDeviceToHost, c->stream), "read K");
+  RE_CUDA(c, cudaMemcpyAsync(out_econs(c), c->s.econs, 8 * R, cudaMemcpyDeviceToHost, c->stream),
+          "read econs");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  int rc = status_eval(c, out_status(c));
+  if (rc) return rc;
+  const double *u = out_U(c), *k = out_K(c), *e = out_econs(c);
   for (size_t r = 0; r < R; ++r) {
     if (U) U[r] = u[r];
     if (K) K[r] = k[r];
@@ -1274,6 +1299,7 @@ void re_destroy(re_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ring) cudaFreeHost(c->h_ring);
+  if (c->h_out) cudaFreeHost(c->h_out);
   for (int k = 0; k < kRing; ++k)
     if (c->ring_ev[k]) cudaEventDestroy(c->ring_ev[k]);
   delete c;
