@@ -368,6 +368,31 @@ def run_gpu(args, cfg):
     h2d = 4 * Rtot
     d2h = 4 * Rtot + Rtot + 3 * 8 * Rtot + 4 * Rtot
 
+    # ---- the asynchronous scheme (Implementation section) on the same workload:
+    # one free-running launch, exchanges decided inside it by the rotating
+    # master after N_x of its own steps; no replica waits for the slowest
+    free = None
+    if args.free_attempts > 0:
+        nxf = max(nx, 1)
+        try:
+            ctx.run_free(2, nxf)
+            torch.cuda.synchronize()
+            s0 = ctx.counters()[0].astype(np.float64)
+            fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fe0.record(stream)
+            ctx.run_free(args.free_attempts, nxf)
+            fe1.record(stream)
+            torch.cuda.synchronize()
+            dsteps = ctx.counters()[0].astype(np.float64) - s0
+            Ns = np.concatenate([[N] * R for (N, R, _, _) in ens_spec])
+            _, fval = aggregate(fe0.elapsed_time(fe1) / 1e3, float((Ns * dsteps).sum()), ws, dist)
+            free = {"value": fval, "unit": "replica·atom-steps/s",
+                    "mode": "free-running: one launch, in-launch exchanges (rotating master)",
+                    "attempts": args.free_attempts, "nx": nxf,
+                    "mean_steps_per_attempt": float(dsteps.sum() / (Rtot * args.free_attempts))}
+        except re.REError as e:
+            free = {"unavailable": str(e)}
+
     # ---- plain FP64 one-replica-per-launch path on the same workload (bounded)
     plain = None
     if len(ens_spec) == 1 and rank == 0 and not args.no_plain:
@@ -424,6 +449,7 @@ def run_gpu(args, cfg):
             "cpu_baseline": cpu,
             "e2e": {"value": ws * e2e_work / t_e2e, "unit": "replica·atom-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "async": free,
             "gpu_launches": 2 * K,
             "clocks": clocks,
         }
@@ -678,6 +704,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--free-attempts", type=int, default=200,
+                    help="exchange attempts of the free-running measurement (0: skip)")
     ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion"],
                     help="run a study instead of the throughput bench")
     ap.add_argument("--lam-n", type=int, default=864)
