@@ -385,10 +385,11 @@ def run_gpu(args, cfg):
             torch.cuda.synchronize()
             dsteps = ctx.counters()[0].astype(np.float64) - s0
             Ns = np.concatenate([[N] * R for (N, R, _, _) in ens_spec])
-            _, fval = aggregate(fe0.elapsed_time(fe1) / 1e3, float((Ns * dsteps).sum()), ws, dist)
+            ft, fval = aggregate(fe0.elapsed_time(fe1) / 1e3, float((Ns * dsteps).sum()), ws, dist)
             free = {"value": fval, "unit": "replica·atom-steps/s",
                     "mode": "free-running: one launch, in-launch exchanges (rotating master)",
                     "attempts": args.free_attempts, "nx": nxf,
+                    "exch_per_s": ws * len(ens_spec) * args.free_attempts / ft,
                     "mean_steps_per_attempt": float(dsteps.sum() / (Rtot * args.free_attempts))}
         except re.REError as e:
             free = {"unavailable": str(e)}
