@@ -441,6 +441,7 @@ def run_gpu(args, cfg):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": profiled_traffic(args.config, tuned, prec),
+                         "ncu_pipes": (profiled_record(args.config, tuned, prec) or {}).get("pipes"),
                          "kernel": f"md_batched_kernel<{prec}>",
                          "peak_source": "FP64 nominal 1.25 TFLOP/s" if prec == "fp64" else
                                         "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
@@ -669,7 +670,12 @@ def run_diffusion(args):
 # valid only while the kernel's sources are the ones that were profiled.
 PROFILED_TRAFFIC = {
     ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "bd1533beafd5c35e",
-                                 "bytes_per_launch": 14035968 + 5120},
+                                 "bytes_per_launch": 14035968 + 5120,
+                                 # pipe use over the SMs' active cycles (ncu --set full)
+                                 "pipes": {"fma_pct": 25.77, "alu_pct": 38.32, "fp64_pct": 5.51,
+                                           "issue_active_pct": 60.64,
+                                           "smem_wavefronts": 20908454,
+                                           "smem_bank_conflicts": 8653888}},
 }
 
 
@@ -684,15 +690,21 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config, launch, prec):
-    """ncu DRAM traffic per launch for this workload, or None when the kernel
+def profiled_record(config, launch, prec):
+    """The ncu capture of this workload's launch shape, or None when the kernel
     changed since the capture (or this shape was not captured)."""
     key = (config, (launch.get("cluster"), launch.get("atom_threads"), launch.get("cell_div")),
            prec)
     rec = PROFILED_TRAFFIC.get(key)
     if rec is None or rec["kernel_sha256_16"] != kernel_sources_hash():
         return None
-    return rec["bytes_per_launch"]
+    return rec
+
+
+def profiled_traffic(config, launch, prec):
+    """ncu DRAM traffic per launch for this workload, or None (see profiled_record)."""
+    rec = profiled_record(config, launch, prec)
+    return None if rec is None else rec["bytes_per_launch"]
 
 
 def main():
