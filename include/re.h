@@ -212,6 +212,22 @@ int re_get_state(re_ctx *c, double *x, double *v);
 /* Replaces positions and velocities (same layout); lists and forces are
  * recomputed before the next step.  Step counters are unchanged. */
 int re_set_state(re_ctx *c, const double *x, const double *v);
+/* Checkpoint and resume.  A checkpoint holds everything the next call reads:
+ * the fixed-point positions, velocities and forces, the neighbour lists and
+ * their reference positions, the atom order, per replica T, lam, U, K, econs,
+ * the pending exchange factors, step and rebuild counters, per ensemble the
+ * exchange-attempt counter and per ladder pair the statistics, and the
+ * launch configuration.  The random numbers are counter-based (Philox keyed
+ * by seed and replica, counted by step and attempt), so a context restored
+ * from a checkpoint continues bit for bit as the original would have.
+ * re_checkpoint_size gives the bytes; re_checkpoint_save writes them into a
+ * caller-owned host buffer of at least that size (synchronises the stream);
+ * re_checkpoint_load restores them into a context created with the same
+ * ensembles, seed and options (RE_EINVAL if the buffer is not a checkpoint of
+ * a context of that shape; the context is unchanged then). */
+int re_checkpoint_size(const re_ctx *c, size_t *bytes);
+int re_checkpoint_save(re_ctx *c, void *buf, size_t bytes);
+int re_checkpoint_load(re_ctx *c, const void *buf, size_t bytes);
 /* Forces at the current positions (host, 3 * atoms). */
 int re_forces(re_ctx *c, double *f);
 /* Per replica steps done and list rebuilds done (host, n_rep each; may be NULL). */

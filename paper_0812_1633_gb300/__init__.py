@@ -74,6 +74,9 @@ def lib():
         L.re_get_state.argtypes = [vp, dp, dp]
         L.re_set_state.argtypes = [vp, dp, dp]
         L.re_forces.argtypes = [vp, dp]
+        L.re_checkpoint_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.re_checkpoint_save.argtypes = [vp, vp, C.c_size_t]
+        L.re_checkpoint_load.argtypes = [vp, vp, C.c_size_t]
         L.re_counters.argtypes = [vp, i64p, i64p]
         L.re_accept_stats.argtypes = [vp, i64p, i64p]
         L.re_info.argtypes = [vp, C.POINTER(C.c_int), i64p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -266,6 +269,22 @@ class Context:
             v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.n_atoms, 3)
             vp = _p(v, C.c_double)
         _check(lib().re_set_state(self._h, xp, vp), self._h)
+
+    def checkpoint(self):
+        """Everything the next call reads, as a host byte array (numpy uint8):
+        restoring it into a context created with the same arguments continues
+        the run bit for bit."""
+        n = C.c_size_t(0)
+        _check(lib().re_checkpoint_size(self._h, C.byref(n)), self._h)
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib().re_checkpoint_save(self._h, buf.ctypes.data_as(C.c_void_p), n.value), self._h)
+        return buf
+
+    def restore(self, buf):
+        """Loads a checkpoint taken from a context of the same shape, seed and
+        options (raises REError with RE_EINVAL otherwise)."""
+        b = np.ascontiguousarray(np.frombuffer(memoryview(buf), np.uint8))
+        _check(lib().re_checkpoint_load(self._h, b.ctypes.data_as(C.c_void_p), b.size), self._h)
 
     def forces(self):
         f = np.zeros((self.n_atoms, 3))

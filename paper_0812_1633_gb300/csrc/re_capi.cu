@@ -1083,6 +1083,152 @@ int re_set_state(re_ctx* c, const double* x, const double* v) {
   return status_check(c);
 }
 
+namespace {
+
+// A checkpoint: this header, then the arrays of ckpt_arrays() in order.
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, precision, path, n_ens;
+  int32_t n_rep, n_pairs, plain_refresh, pad;
+  int64_t n_atoms, n_nbr, since_sort, payload;
+  LaunchCfg cfg;
+  uint64_t shape;  // hash of the ensembles' parameters and the replica table
+};
+constexpr char kCkptMagic[8] = {'R', 'E', '-', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptArray {
+  void* dev;
+  size_t bytes;
+};
+
+// Everything the next call reads (scratch buffers and per-launch words excluded).
+std::vector<CkptArray> ckpt_arrays(re_ctx* c) {
+  const size_t A = (size_t)c->n_atoms, R = (size_t)c->n_rep, E = c->ens.size();
+  const size_t P = (size_t)c->n_pairs;
+  StateDev& s = c->s;
+  return {{s.qx, 8 * A},     {s.qy, 8 * A},      {s.qz, 8 * A},     {s.vx, 8 * A},
+          {s.vy, 8 * A},     {s.vz, 8 * A},      {s.fx, 8 * A},     {s.fy, 8 * A},
+          {s.fz, 8 * A},     {s.rx, 4 * A},      {s.ry, 4 * A},     {s.rz, 4 * A},
+          {s.ncnt, 32 * A},  {s.perm, 4 * A},    {s.nbr, 2 * (size_t)c->n_nbr},
+          {s.T, 8 * R},      {s.U, 8 * R},       {s.K, 8 * R},      {s.econs, 8 * R},
+          {s.vscale, 8 * R}, {s.lam, 8 * R},     {s.fscale, 8 * R}, {s.step, 8 * R},
+          {s.nreb, 8 * R},   {s.status, 4 * R},  {s.valid, 4 * R},  {s.dmax, 4 * R},
+          {s.attempt, 8 * E}, {s.pair_att, 8 * P}, {s.pair_acc, 8 * P}};
+}
+
+// FNV-1a over the parameters that fix the context's shape and trajectories.
+uint64_t ckpt_shape(const re_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  for (const EnsDev& e : c->ens) {
+    const int iv[7] = {e.N, e.R, e.rep_off, e.pair_off, e.cap, e.shift, e.xdist};
+    const double dv[6] = {e.L, e.rc, e.rlist, e.skin, e.dt, e.tau};
+    mix(iv, sizeof iv);
+    mix(e.capsub, sizeof e.capsub);
+    mix(dv, sizeof dv);
+    mix(&e.seed, sizeof e.seed);
+    mix(&e.parity_mode, sizeof e.parity_mode);
+  }
+  for (const RepDev& r : c->reps) {
+    const int64_t v[5] = {r.ens, r.id, r.atom_off, r.stream, r.nbr_off};
+    mix(v, sizeof v);
+  }
+  const int ov[3] = {c->opt.shift_energy, c->opt.sort_interval, c->opt.nx};
+  mix(ov, sizeof ov);
+  return h;
+}
+
+size_t ckpt_bytes(re_ctx* c) {
+  size_t n = sizeof(CkptHeader);
+  for (const CkptArray& a : ckpt_arrays(c)) n += a.bytes;
+  return n;
+}
+
+}  // namespace
+
+int re_checkpoint_size(const re_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(const_cast<re_ctx*>(c), RE_EINVAL, "bad arguments");
+  *bytes = ckpt_bytes(const_cast<re_ctx*>(c));
+  return RE_OK;
+}
+
+int re_checkpoint_save(re_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return fail(c, RE_EINVAL, "bad arguments");
+  const size_t need = ckpt_bytes(c);
+  if (bytes < need) return fail(c, RE_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, need);
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+  h.version = 1;
+  h.precision = (uint32_t)c->opt.precision;
+  h.path = (uint32_t)c->opt.path;
+  h.n_ens = (uint32_t)c->ens.size();
+  h.n_rep = c->n_rep;
+  h.n_pairs = c->n_pairs;
+  h.plain_refresh = c->plain_refresh ? 1 : 0;
+  h.n_atoms = c->n_atoms;
+  h.n_nbr = c->n_nbr;
+  h.since_sort = c->since_sort;
+  h.payload = (int64_t)(need - sizeof h);
+  h.cfg = c->cfg;
+  h.shape = ckpt_shape(c);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memcpy(out, &h, sizeof h);
+  size_t off = sizeof h;
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  for (const CkptArray& a : ckpt_arrays(c)) {
+    if (a.bytes)
+      RE_CUDA(c, cudaMemcpy(out + off, a.dev, a.bytes, cudaMemcpyDeviceToHost), "checkpoint read");
+    off += a.bytes;
+  }
+  return RE_OK;
+}
+
+int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return fail(c, RE_EINVAL, "bad arguments");
+  CkptHeader h{};
+  if (bytes < sizeof h) return fail(c, RE_EINVAL, "not a checkpoint (%zu bytes)", bytes);
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, kCkptMagic, sizeof h.magic) != 0 || h.version != 1)
+    return fail(c, RE_EINVAL, "not a checkpoint of this library");
+  if (h.precision != (uint32_t)c->opt.precision || h.path != (uint32_t)c->opt.path ||
+      h.n_ens != (uint32_t)c->ens.size() || h.n_rep != c->n_rep || h.n_pairs != c->n_pairs ||
+      h.n_atoms != c->n_atoms || h.n_nbr != c->n_nbr || h.shape != ckpt_shape(c))
+    return fail(c, RE_EINVAL, "checkpoint of a context of another shape, seed or options");
+  if (h.payload < 0 || bytes < sizeof h + (size_t)h.payload || ckpt_bytes(c) != sizeof h + (size_t)h.payload)
+    return fail(c, RE_EINVAL, "truncated checkpoint");
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  // the launch configuration first: it fixes the cells and the lists' layout
+  const int old_div = c->cfg.cell_div;
+  apply_cells(c, h.cfg.cell_div);
+  int rc = check_cfg(c, h.cfg);
+  if (rc) {
+    apply_cells(c, old_div);
+    return rc;
+  }
+  c->cfg = h.cfg;
+  c->resident_clusters = -1;
+  rc = upload_tables(c);
+  if (rc) return rc;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  size_t off = sizeof h;
+  for (const CkptArray& a : ckpt_arrays(c)) {
+    if (a.bytes)
+      RE_CUDA(c, cudaMemcpy(a.dev, in + off, a.bytes, cudaMemcpyHostToDevice), "checkpoint write");
+    off += a.bytes;
+  }
+  c->since_sort = h.since_sort;
+  c->plain_refresh = h.plain_refresh != 0;
+  RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  return RE_OK;
+}
+
 int re_forces(re_ctx* c, double* f) {
   if (!c || !f) return fail(c, RE_EINVAL, "bad arguments");
   int rc = status_check(c);
