@@ -3,6 +3,7 @@
 // captured in a CUDA graph), getters, the autotuner and the stateless entry
 // points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -15,6 +16,15 @@
 
 #include "re.h"
 #include "re_internal.h"
+
+namespace {
+// An NVTX range over one API call (shown by nsys / ncu timelines; header-only
+// NVTX costs nothing when no tool is attached).
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 using re::EnsDev;
 using re::finish_ens;
@@ -715,6 +725,7 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
 }
 
 int re_advance(re_ctx* c, const int32_t* steps) {
+  ApiRange range_("re_advance");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (!steps) return launch_advance(c, c->d_budget_nx, nullptr, c->opt.nx);
   for (int r = 0; r < c->n_rep; ++r)
@@ -735,6 +746,7 @@ int re_advance(re_ctx* c, const int32_t* steps) {
 }
 
 int re_advance_async(re_ctx* c, int nx) {
+  ApiRange range_("re_advance_async");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (nx < 1) return fail(c, RE_EINVAL, "nx must be >= 1");
   if (c->opt.path != RE_PATH_BATCHED)
@@ -745,6 +757,7 @@ int re_advance_async(re_ctx* c, int nx) {
 
 int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
                 int32_t* log_partner, uint8_t* log_acc) {
+  ApiRange range_("re_run_free");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (n_att < 0 || nx < 1) return fail(c, RE_EINVAL, "n_att >= 0 and nx >= 1 required");
   if (c->opt.path != RE_PATH_BATCHED)
@@ -823,6 +836,7 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
 }
 
 int re_run_async(re_ctx* c, int n_cycles, int nx, int use_graph) {
+  ApiRange range_("re_run_async");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (n_cycles < 0 || nx < 1) return fail(c, RE_EINVAL, "n_cycles >= 0 and nx >= 1 required");
   if (c->opt.path != RE_PATH_BATCHED)
@@ -869,6 +883,7 @@ int re_run_async(re_ctx* c, int n_cycles, int nx, int use_graph) {
 }
 
 int re_exchange(re_ctx* c, int32_t* partner_out, uint8_t* accepted_out) {
+  ApiRange range_("re_exchange");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r, c->d_partner,
                                       c->d_acc, c->stream);
@@ -888,6 +903,7 @@ int re_exchange(re_ctx* c, int32_t* partner_out, uint8_t* accepted_out) {
 }
 
 int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
+  ApiRange range_("re_run");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (n_cycles < 0) return fail(c, RE_EINVAL, "n_cycles must be >= 0");
   if (n_cycles == 0) return RE_OK;
@@ -979,6 +995,7 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
 }
 
 int re_energies(re_ctx* c, double* U, double* K, double* H) {
+  ApiRange range_("re_energies");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   // status and energies in one synchronisation (pinned destinations)
   const size_t R = (size_t)c->n_rep;
@@ -1156,6 +1173,7 @@ int re_checkpoint_size(const re_ctx* c, size_t* bytes) {
 }
 
 int re_checkpoint_save(re_ctx* c, void* buf, size_t bytes) {
+  ApiRange range_("re_checkpoint_save");
   if (!c || !buf) return fail(c, RE_EINVAL, "bad arguments");
   const size_t need = ckpt_bytes(c);
   if (bytes < need) return fail(c, RE_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", bytes, need);
@@ -1187,6 +1205,7 @@ int re_checkpoint_save(re_ctx* c, void* buf, size_t bytes) {
 }
 
 int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
+  ApiRange range_("re_checkpoint_load");
   if (!c || !buf) return fail(c, RE_EINVAL, "bad arguments");
   CkptHeader h{};
   if (bytes < sizeof h) return fail(c, RE_EINVAL, "not a checkpoint (%zu bytes)", bytes);
@@ -1295,6 +1314,7 @@ int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div, int* a
 }
 
 int re_autotune(re_ctx* c, int steps) {
+  ApiRange range_("re_autotune");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
   if (c->opt.path != RE_PATH_BATCHED) return RE_OK;
   // each trial starts with a full list build; enough steps that it does not dominate
