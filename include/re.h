@@ -41,6 +41,7 @@
 #ifndef RE_GB300_H
 #define RE_GB300_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

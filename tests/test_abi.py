@@ -61,3 +61,18 @@ def test_default_opts_match_paper():
     o = re.default_opts()
     assert o["dt"] == 0.005 and o["skin"] == 0.5   # time step 0.005, list radius 3.0 = 2.5 + 0.5
     assert o["shift_energy"] == 1 and o["precision"] == re.PREC["mixed"]
+
+
+def test_header_compiles_as_c99(tmp_path):
+    """include/re.h is a plain C header: it compiles with a C99 compiler on its own."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_re.c"
+    src.write_text('#include "re.h"\n'
+                   "int main(void) { size_t n = 0; re_opts o; re_default_opts(&o);\n"
+                   "  return re_checkpoint_size(0, &n) == RE_OK; }\n")
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           "-c", str(src), "-o", str(tmp_path / "use_re.o")])
