@@ -598,6 +598,60 @@ def run_lambda(args):
     print(json.dumps(out), flush=True)
 
 
+def run_acceptance(args):
+    """Exchange acceptance on the paper's workload (Example section: 4000 atoms,
+    rho 0.8442, T_k = 0.7 * 1.0275^k) explained by the model's heat capacity:
+    the replicas run without exchanges; the configurational heat capacity per
+    atom comes from the potential-energy fluctuations, Var(U) / (N T^2), and
+    independently from the slope d<U>/dT over the ladder; the acceptance of each
+    neighbouring pair is predicted from the sampled energies alone, the mean of
+    min(1, exp((1/T_a - 1/T_b)(U_a - U_b))) over pairs of samples, and compared
+    with the acceptance the exchanges then measure."""
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    build.build()
+    N, R = 4000, args.acc_r
+    temps = inputs.paper_ladder(R)
+    ctx = melted_context(re, N, temps, 4242, skin=0.5)
+    for _ in range(40):
+        ctx.advance(500)
+    S, stride = args.acc_samples, 25
+    U = np.zeros((S, R))
+    for s in range(S):
+        ctx.advance(stride)
+        U[s] = ctx.energies()[0]
+    mean, var = U.mean(0), U.var(0)
+    blocks = U[:S - S % 20].reshape(20, -1, R).mean(1)
+    err = blocks.std(0, ddof=1) / np.sqrt(20)
+    pred = []
+    for k in range(R - 1):
+        a = 1.0 / temps[k] - 1.0 / temps[k + 1]
+        d = a * (U[:, k][:, None] - U[:, k + 1][None, ::7])
+        pred.append(float(np.minimum(1.0, np.exp(np.minimum(d, 0.0))).mean()))
+    # then the exchanges themselves
+    att0, acc0 = ctx.accept_stats()
+    for _ in range(args.acc_attempts):
+        ctx.advance(10)
+        ctx.exchange()
+    att, acc = ctx.accept_stats()
+    att, acc = att - att0, acc - acc0
+    out = {"study": "exchange acceptance vs heat capacity",
+           "workload": f"{R} replicas x {N} atoms, rho 0.8442, T_k = 0.7 * 1.0275^k, skin 0.5, "
+                       f"mixed, melted start; {S} samples every {stride} steps without exchanges, "
+                       f"then {args.acc_attempts} attempts every 10 steps",
+           "T": temps.tolist(), "U_per_atom": (mean / N).tolist(),
+           "U_err_per_atom": (err / N).tolist(),
+           "C_conf_from_fluctuations": (var / (N * temps ** 2)).tolist(),
+           "C_conf_from_slope": float(np.polyfit(temps, mean, 1)[0] / N),
+           "acceptance_predicted_per_pair": pred,
+           "acceptance_predicted_mean": float(np.mean(pred)),
+           "acceptance_measured_per_pair": (acc / np.maximum(att, 1)).tolist(),
+           "acceptance_measured_mean": float(acc.sum() / max(att.sum(), 1))}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def msd_diffusion(logT, steps, max_lag=10):
     """D of ln T: half the slope of the mean squared displacement of ln T against
     elapsed steps, over lags of 1..max_lag attempts (least squares through 0).
@@ -719,7 +773,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--free-attempts", type=int, default=200,
                     help="exchange attempts of the free-running measurement (0: skip)")
-    ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion"],
+    ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion", "acceptance"],
                     help="run a study instead of the throughput bench")
     ap.add_argument("--lam-n", type=int, default=864)
     ap.add_argument("--lam-nx", type=int, default=5)
@@ -731,6 +785,9 @@ def main():
     ap.add_argument("--dif-attempts", type=int, default=2000)
     ap.add_argument("--dif-nx", default="1,2,5,10,20")
     ap.add_argument("--dif-cluster", type=int, default=2)
+    ap.add_argument("--acc-r", type=int, default=8)
+    ap.add_argument("--acc-samples", type=int, default=4000)
+    ap.add_argument("--acc-attempts", type=int, default=2000)
     ap.add_argument("--drift-n", type=int, default=4000)
     ap.add_argument("--drift-r", type=int, default=8)
     ap.add_argument("--drift-steps", type=int, default=20000)
@@ -749,6 +806,9 @@ def main():
         return
     if args.study == "diffusion":
         run_diffusion(args)
+        return
+    if args.study == "acceptance":
+        run_acceptance(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)
