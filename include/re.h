@@ -246,9 +246,9 @@ int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *a
 /* re_config and whether the neighbour lists are kept in shared memory. */
 int re_config_ex(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads,
                  int *lists_smem);
-/* Times candidate launch configurations (cluster, atom_threads, cell_div) over
- * `steps` steps each on a copy of the state and keeps the fastest; the state
- * is restored afterwards. */
+/* Times candidate launch configurations (cluster, atom_threads, cell_div and
+ * the lists' placement, global or shared memory) over `steps` steps each on a
+ * copy of the state and keeps the fastest; the state is restored afterwards. */
 int re_autotune(re_ctx *c, int steps);
 /* Queues subsequent work on stream (a cudaStream_t; NULL: legacy default). */
 int re_set_stream(re_ctx *c, void *stream);
