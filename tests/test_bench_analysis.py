@@ -50,3 +50,14 @@ def test_diffusion_estimator_recovers_a_known_coefficient():
     y = np.cumsum(rng.normal(0.0, np.sqrt(2 * D * ds)), axis=0)
     got = bench.msd_diffusion(np.exp(y), steps)
     assert abs(got - D) < 0.05 * D
+
+
+def test_drift_slope_estimator_recovers_known_slopes():
+    # H~/N rising linearly in time at a known rate per replica, plus noise
+    rng = np.random.default_rng(11)
+    N, R = 4000, 5
+    t = np.arange(0.0, 100.0, 0.5)
+    rates = np.array([1e-6, -2e-6, 0.0, 5e-7, 3e-6])
+    H = N * (rates[None, :] * t[:, None] + rng.normal(0.0, 1e-7, (t.size, R))) - 5.0 * N
+    got = bench.drift_slopes(t, H, N)
+    assert np.allclose(got, rates, atol=5e-9)
