@@ -365,6 +365,7 @@ def run_gpu(args, cfg):
         ctx.energies()
     t_e2e = time.perf_counter() - t_e2e0
     e2e_work = sum(atoms_per_cycle(cfg, budgets[W + (k % K)]) for k in range(nE))
+    _, e2e_value = aggregate(t_e2e, e2e_work, ws, dist)  # slowest rank's time, all ranks' work
     h2d = 4 * Rtot
     d2h = 4 * Rtot + Rtot + 3 * 8 * Rtot + 4 * Rtot
 
@@ -374,6 +375,8 @@ def run_gpu(args, cfg):
     free = None
     if args.free_attempts > 0:
         nxf = max(nx, 1)
+        ft_local = fwork_local = dsum = 0.0
+        why = None
         try:
             ctx.run_free(2, nxf)
             torch.cuda.synchronize()
@@ -385,14 +388,27 @@ def run_gpu(args, cfg):
             torch.cuda.synchronize()
             dsteps = ctx.counters()[0].astype(np.float64) - s0
             Ns = np.concatenate([[N] * R for (N, R, _, _) in ens_spec])
-            ft, fval = aggregate(fe0.elapsed_time(fe1) / 1e3, float((Ns * dsteps).sum()), ws, dist)
+            ft_local, fwork_local = fe0.elapsed_time(fe1) / 1e3, float((Ns * dsteps).sum())
+            dsum = float(dsteps.sum())
+        except re.REError as e:
+            why = str(e)
+        # every rank reaches this collective: all of them go on, or none
+        failed = why is not None
+        if dist is not None and ws > 1:
+            flag = torch.tensor([1.0 if failed else 0.0], dtype=torch.float64)
+            if dist.get_backend() == "nccl":
+                flag = flag.cuda()
+            dist.all_reduce(flag, op=dist.ReduceOp.MAX)
+            failed = flag.item() > 0
+        if failed:
+            free = {"unavailable": why or "free-running launch refused on another rank"}
+        else:
+            ft, fval = aggregate(ft_local, fwork_local, ws, dist)
             free = {"value": fval, "unit": "replica·atom-steps/s",
                     "mode": "free-running: one launch, in-launch exchanges (rotating master)",
                     "attempts": args.free_attempts, "nx": nxf,
                     "exch_per_s": ws * len(ens_spec) * args.free_attempts / ft,
-                    "mean_steps_per_attempt": float(dsteps.sum() / (Rtot * args.free_attempts))}
-        except re.REError as e:
-            free = {"unavailable": str(e)}
+                    "mean_steps_per_attempt": dsum / (Rtot * args.free_attempts)}
 
     # ---- plain FP64 one-replica-per-launch path on the same workload (bounded)
     plain = None
@@ -449,7 +465,7 @@ def run_gpu(args, cfg):
                                         f"pairs per atom-step"},
             "plain_fp64": plain,
             "cpu_baseline": cpu,
-            "e2e": {"value": ws * e2e_work / t_e2e, "unit": "replica·atom-steps/s",
+            "e2e": {"value": e2e_value, "unit": "replica·atom-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "async": free,
             "gpu_launches": 2 * K,
