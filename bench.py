@@ -276,7 +276,12 @@ def run_gpu(args, cfg):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    build.build()
+    # one rank per node compiles (when the library is out of date); the others
+    # wait, so that no two processes write the same object files
+    if local == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
     re.lib()
     desc, ens_spec, nx, skin, mode, prec = cfg
     seed = rank_seed(rank)
