@@ -103,3 +103,41 @@ def test_foreign_checkpoints_are_refused(re):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     for ctx in victims + [a, twin]:
         ctx.close()
+
+
+def test_group_resume_is_bit_exact(re):
+    """A group of uneven ensembles (one launch) resumes bit for bit too."""
+    specs = [(256, 3, 0.7, 1.6), (500, 2, 0.8, 1.4)]
+
+    def group():
+        members = [re.Context(n, inputs.box_length(n), 2.5, inputs.geometric_ladder(t0, t1, r),
+                              50 + k, skin=0.3, sort_interval=20)
+                   for k, (n, r, t0, t1) in enumerate(specs)]
+        g = re.Context.group(members)
+        for m in members:
+            m.close()
+        return g
+
+    bud = inputs.random_budgets(5, 6, 5, 15, 9)
+    a = group()
+    for c in range(2):
+        a.advance(bud[c])
+        a.exchange()
+    ck = a.checkpoint()
+
+    def rest(ctx):
+        dec = []
+        for c in range(2, 6):
+            ctx.advance(bud[c])
+            dec.append(ctx.exchange(outputs=True))
+        x, v = ctx.get_state()
+        return dict(x=x, v=v, T=ctx.temps(), U=ctx.energies()[0], steps=ctx.counters()[0],
+                    att=ctx.accept_stats()[0], partners=np.array([d[0] for d in dec]),
+                    accepted=np.array([d[1] for d in dec]))
+
+    ra = rest(a)
+    b = group()
+    b.restore(ck)
+    assert_same(ra, rest(b))
+    a.close()
+    b.close()
