@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 from paper_0812_1633_gb300 import inputs  # noqa: E402
 
 CONFIGS = {
-    # name: (description, list of ensembles (N, R, t_min, t_max), nx, skin, budget mode)
+    # name: (description, list of ensembles (N, R, t_min, t_max), nx, skin, budget mode,
+    # precision); skin "auto": chosen by measurement (paper_0812_1633_gb300.tune)
     "c0": ("8 replicas x 256 atoms, rho 0.8442, T 0.8-1.6 geometric, N_x 100",
            [(256, 8, 0.8, 1.6)], 100, 0.5, "fixed", "fp64"),
     "c1": ("64 replicas x 864 atoms, rho 0.8442, T 0.7-2.0 geometric, N_x 10, skin 0.3",
@@ -41,11 +42,11 @@ CONFIGS = {
     "c2": ("5 ensembles in one launch: 16x256, 32x500, 48x864, 64x2048, 96x4000 atoms, T 0.7-2.5, "
            "budgets uniform 5-50 per replica per attempt",
            [(256, 16, 0.7, 2.5), (500, 32, 0.7, 2.5), (864, 48, 0.7, 2.5), (2048, 64, 0.7, 2.5),
-            (4000, 96, 0.7, 2.5)], 0, 0.5, "random", "mixed"),
+            (4000, 96, 0.7, 2.5)], 0, "auto", "random", "mixed"),
     "c3": ("256 replicas x 4000 atoms, rho 0.8442, T 0.75-1.8 geometric, N_x 10",
            [(4000, 256, 0.75, 1.8)], 10, 0.5, "fixed", "mixed"),
     "c4": ("1024 replicas x 2048 atoms, rho 0.8442, T 0.7-3.0 geometric, N_x 1",
-           [(2048, 1024, 0.7, 3.0)], 1, 0.5, "fixed", "mixed"),
+           [(2048, 1024, 0.7, 3.0)], 1, "auto", "fixed", "mixed"),
 }
 FLOPS_PER_PAIR = 37.0   # unique pair: 34 for the pair itself + 3 for the reaction
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
@@ -81,6 +82,12 @@ def aggregate(total_s, work, ws, dist=None):
     return total_s, work / total_s
 
 
+def oracle_skin(cfg):
+    """The oracle's skin for a workload: its own, or 0.5 (the paper's list
+    radius 3.0) where the GPU path chooses it by measurement."""
+    return 0.5 if cfg[3] == "auto" else cfg[3]
+
+
 def make_budgets(cfg, R, cycles, seed):
     _, ens, nx, _, mode, _ = cfg
     if mode == "random":
@@ -101,7 +108,7 @@ def oracle_rate(cfg, seed, wall_target=10.0, max_steps=2000):
     ens_list = []
     for i, (N, R, t0, t1) in enumerate(cfg[1]):
         L = inputs.box_length(N)
-        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=cfg[3]))
+        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=oracle_skin(cfg)))
     steps = 2
     done_atoms, spent = 0.0, 0.0
     while True:
@@ -130,7 +137,7 @@ def run_reference(args, cfg):
     ens_list = []
     for i, (N, R, t0, t1) in enumerate(cfg[1]):
         L = inputs.box_length(N)
-        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=cfg[3]))
+        ens_list.append(O.Ensemble(N, L, inputs.geometric_ladder(t0, t1, R), seed + i, skin=oracle_skin(cfg)))
     Rtot = sum(e.R for e in ens_list)
     # each reference step: the whole workload's cycle for small configs; a
     # bounded sample of replicas for large ones (size-normalised metric)
@@ -285,33 +292,37 @@ def run_gpu(args, cfg):
     re.lib()
     desc, ens_spec, nx, skin, mode, prec = cfg
     seed = rank_seed(rank)
-    members = []
-    for i, (N, R, t0, t1) in enumerate(ens_spec):
-        L = inputs.box_length(N)
-        members.append(re.Context(N, L, 2.5, inputs.geometric_ladder(t0, t1, R), seed + i,
-                                  skin=skin, precision=prec, nx=max(nx, 1)))
-    ctx = members[0] if len(members) == 1 else re.Context.group(members)
-    if len(members) > 1:
-        for m in members:
-            m.close()
     stream = torch.cuda.current_stream()
-    ctx.set_stream(stream)
-    if args.launch:
-        cl, at, cd = (int(v) for v in args.launch.split(","))
-        members_kw = dict(cluster=cl, atom_threads=at, cell_div=cd)
-        ctx.close()
+
+    def make(skin_, **kw):
         members = []
         for i, (N, R, t0, t1) in enumerate(ens_spec):
             L = inputs.box_length(N)
             members.append(re.Context(N, L, 2.5, inputs.geometric_ladder(t0, t1, R), seed + i,
-                                      skin=skin, precision=prec, nx=max(nx, 1), **members_kw))
-        ctx = members[0] if len(members) == 1 else re.Context.group(members)
+                                      skin=skin_, precision=prec, nx=max(nx, 1), **kw))
+        c = members[0] if len(members) == 1 else re.Context.group(members)
         if len(members) > 1:
             for m in members:
                 m.close()
-        ctx.set_stream(stream)
+        c.set_stream(stream)
+        return c
+
+    skin_trials = None
+    if skin == "auto" and not args.launch:
+        from paper_0812_1633_gb300 import tune
+        Rtot0 = sum(R for (_, R, _, _) in ens_spec)
+        tb = make_budgets(cfg, Rtot0, 20, 99 + rank) if mode == "random" else None
+        skin, ctx, skin_trials = tune.choose_skin(make, cycles=20, budgets=tb)
         tuned = ctx.config()
     else:
+        skin = 0.5 if skin == "auto" else skin
+        ctx = make(skin)
+    if args.launch:
+        cl, at, cd = (int(v) for v in args.launch.split(","))
+        ctx.close()
+        ctx = make(skin, cluster=cl, atom_threads=at, cell_div=cd)
+        tuned = ctx.config()
+    elif skin_trials is None:
         tuned = ctx.autotune(steps=40)
     Rtot = ctx.n_rep
     W, K = args.warmup, args.steps
@@ -455,7 +466,8 @@ def run_gpu(args, cfg):
             "data": "synthetic (FCC start at rho 0.8442, seeded Philox velocities and budgets)",
             "config": {"workload": desc, "path": f"{prec} batched (one persistent launch per cycle)",
                        "l2": "flushed between timed steps (256 MB write)",
-                       "launch": tuned, "parallelism": f"replicas, {ws} independent ensemble(s)"},
+                       "launch": tuned, "parallelism": f"replicas, {ws} independent ensemble(s)",
+                       "skin": skin, "skin_trials_ms_per_cycle": skin_trials},
             "exch_per_s": exch_per_s,
             "pair_attempts_per_s": exch_per_s * pairs_per_attempt / max(n_ens, 1),
             "advance_ms": statistics.mean(adv_ms), "exchange_ms": statistics.mean(exch_ms),
