@@ -311,8 +311,16 @@ def run_gpu(args, cfg):
     if skin == "auto" and not args.launch:
         from paper_0812_1633_gb300 import tune
         Rtot0 = sum(R for (_, R, _, _) in ens_spec)
-        tb = make_budgets(cfg, Rtot0, 20, 99 + rank) if mode == "random" else None
-        skin, ctx, skin_trials = tune.choose_skin(make, cycles=20, budgets=tb)
+        # the same budgets on every rank, and each candidate's time agreed as the
+        # slowest rank's: every rank keeps the same skin (one workload)
+        tb = make_budgets(cfg, Rtot0, 20, 99) if mode == "random" else None
+        agree = None
+        if dist is not None:
+            def agree(ms):
+                t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                return float(t.item())
+        skin, ctx, skin_trials = tune.choose_skin(make, cycles=20, budgets=tb, agree=agree)
         tuned = ctx.config()
     else:
         skin = 0.5 if skin == "auto" else skin
@@ -385,6 +393,26 @@ def run_gpu(args, cfg):
     h2d = 4 * Rtot
     d2h = 4 * Rtot + Rtot + 3 * 8 * Rtot + 4 * Rtot
 
+    # ---- the same cycles replayed as one captured CUDA graph (re_run with a
+    # graph): the host enqueues one graph instead of two launches per cycle
+    graph = None
+    if mode == "fixed" and args.graph_cycles > 0:
+        nG = args.graph_cycles
+        ctx.run(nG, graph=True)          # capture and a first, untimed replay
+        torch.cuda.synchronize()
+        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ge0.record(stream)
+        ctx.run(nG, graph=True)
+        ge1.record(stream)
+        torch.cuda.synchronize()
+        g_s = ge0.elapsed_time(ge1) / 1e3
+        g_work = nG * atoms_per_cycle(cfg, np.full(Rtot, max(nx, 1)))
+        g_s, g_value = aggregate(g_s, g_work, ws, dist)
+        graph = {"value": g_value, "unit": "replica·atom-steps/s", "cycles": nG,
+                 "ms_per_step": 1e3 * g_s / nG, "eager_ms_per_step": 1e3 * total_s / K,
+                 "saved_ms_per_step": 1e3 * (total_s / K - g_s / nG),
+                 "l2": "not flushed inside the graph (the eager steps flush it)"}
+
     # ---- the asynchronous scheme (Implementation section) on the same workload:
     # one free-running launch, exchanges decided inside it by the rotating
     # master after N_x of its own steps; no replica waits for the slowest
@@ -438,15 +466,15 @@ def run_gpu(args, cfg):
         p.exchange()
         torch.cuda.synchronize()
         pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nP = 2
+        nP = 20  # cycles (about 1.6 s on the 64 x 864 workload)
         pe0.record(stream)
         for k in range(nP):
-            p.advance(budgets[W + k])
+            p.advance(budgets[W + (k % K)])
             p.exchange()
         pe1.record(stream)
         torch.cuda.synchronize()
         pt = pe0.elapsed_time(pe1) / 1e3
-        pw = sum(atoms_per_cycle(cfg, budgets[W + k]) for k in range(nP))
+        pw = sum(atoms_per_cycle(cfg, budgets[W + (k % K)]) for k in range(nP))
         plain = {"value": pw / pt, "unit": "replica·atom-steps/s", "steps": nP,
                  "speedup_of_batched_mixed": value / ws / (pw / pt)}
         p.close()
@@ -485,6 +513,7 @@ def run_gpu(args, cfg):
             "e2e": {"value": e2e_value, "unit": "replica·atom-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "async": free,
+            "graph": graph,
             "gpu_launches": 2 * K,
             "clocks": clocks,
         }
@@ -700,6 +729,30 @@ def msd_diffusion(logT, steps, max_lag=10):
     return float((lags * msd).sum() / (lags * lags).sum() / 2.0)
 
 
+def diffusion_sync_trajectory(ctx, nx, attempts):
+    """Synchronous scheme: every attempt, each replica advances nx steps and
+    the ladder attempts its exchanges.  Returns the temperature of every
+    replica after each attempt and the steps it has made since the start
+    (both (attempts, replicas))."""
+    base = ctx.counters()[0]
+    Ts, st = [], []
+    for _ in range(attempts):
+        ctx.advance(nx)
+        ctx.exchange()
+        Ts.append(ctx.temps())
+        st.append(ctx.counters()[0] - base)
+    return np.array(Ts), np.array(st, dtype=np.float64)
+
+
+def diffusion_async_trajectory(ctx, nx, attempts):
+    """Asynchronous scheme (one free-running launch, rotating master after nx
+    of its own steps): the log's temperature after each attempt and the step
+    at which each replica took part, counted from the start."""
+    base = ctx.counters()[0]
+    steps, T, _, _ = ctx.run_free(attempts, nx, log=True)
+    return T, (steps - base).astype(np.float64)
+
+
 def run_diffusion(args):
     """Diffusion coefficient of ln T against the observed exchange stride <N_x>
     (Example section, Diffusion in temperature space) for the synchronous and
@@ -723,26 +776,18 @@ def run_diffusion(args):
         # one launch shape for both schemes, with every replica resident
         shape = dict(skin=0.3, nx=nx, cluster=args.dif_cluster, atom_threads=1)
         ctx = melted_context(re, N, temps, 4242, **shape)
-        base = ctx.counters()[0]
-        Ts, st = [], []
-        for k in range(A):
-            ctx.advance(nx)
-            ctx.exchange()
-            Ts.append(ctx.temps())
-            st.append(ctx.counters()[0] - base)
+        Ts, st = diffusion_sync_trajectory(ctx, nx, A)
         att, acc = ctx.accept_stats()
-        row["sync"] = {"D": msd_diffusion(np.array(Ts), np.array(st)), "mean_nx": nx,
+        row["sync"] = {"D": msd_diffusion(Ts, st), "mean_nx": nx,
                        "acceptance": float(acc.sum() / att.sum())}
         ctx.close()
         ctx = melted_context(re, N, temps, 4242, **shape)
         try:
             a0, c0 = ctx.accept_stats()
-            base = ctx.counters()[0]
-            steps, T, _, _ = ctx.run_free(A, nx, log=True)
+            T, steps = diffusion_async_trajectory(ctx, nx, A)
             att, acc = ctx.accept_stats()
-            steps = steps - base
             mean_nx = float(np.diff(np.vstack([np.zeros((1, R)), steps]), axis=0).mean())
-            row["async"] = {"D": msd_diffusion(T, steps.astype(np.float64)), "mean_nx": mean_nx,
+            row["async"] = {"D": msd_diffusion(T, steps), "mean_nx": mean_nx,
                             "acceptance": float((acc - c0).sum() / (att - a0).sum())}
         except re.REError as e:
             row["async"] = {"unavailable": str(e)}
@@ -804,6 +849,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--graph-cycles", type=int, default=20,
+                    help="cycles of the CUDA-graph replay measurement (0: skip)")
     ap.add_argument("--free-attempts", type=int, default=200,
                     help="exchange attempts of the free-running measurement (0: skip)")
     ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion", "acceptance"],

@@ -165,18 +165,38 @@ int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
  * ends.
  *
  * Requires the batched path and all replicas resident on the GPU at once
- * (RE_EINVAL otherwise).  Every device wait is bounded (about 1 s); a wait
- * that gives up ends the launch with RE_ETIMEOUT, reported here when logging
- * or by the next getter.  The number of steps each replica makes is decided
+ * (RE_EINVAL otherwise).  Every device wait is bounded (1 s by default,
+ * re_set_wait_limit); a wait that gives up ends the launch with RE_ETIMEOUT,
+ * reported here when logging or by the next getter.  The launch then leaves
+ * every replica at a step boundary with a consistent state: an exchange pair
+ * has swapped on both sides or on neither, and T stays a permutation of the
+ * ladder.  Once reported, the timeout marks are cleared and the context goes
+ * on with the next call.  The number of steps each replica makes is decided
  * at run time; re_counters reports them.
  *
  * log_step, log_T (n_att x n_rep, row a = this call's attempt a): the
- * replica's step count when it took part, and its temperature afterwards;
- * log_partner: partner member id (-1 unpaired); log_acc: 1 if accepted.  Any
- * non-NULL log pointer makes the call synchronous; with all NULL it is
- * asynchronous. */
+ * replica's step count when it took part (-1: it did not take part, the
+ * launch having ended before), and its temperature afterwards; log_partner:
+ * partner member id (-1 unpaired); log_acc: 1 if accepted.  Any non-NULL log
+ * pointer makes the call synchronous; with all NULL it is asynchronous.  The
+ * log is written also when the call returns RE_ETIMEOUT. */
 int re_run_free(re_ctx *c, int n_att, int nx, int64_t *log_step, double *log_T,
                 int32_t *log_partner, uint8_t *log_acc);
+
+/* Limit of every bounded device wait of re_run_free (the master's collection
+ * of temperatures, a replica's wait for its partner's pair message), in
+ * seconds of the GPU's global timer: [1e-4, 10], default 1.  The paper's
+ * blocking calls (Implementation section) become these waits. */
+int re_set_wait_limit(re_ctx *c, double seconds);
+
+/* Host-side fault injection for failure detection: in the next re_run_free
+ * call (one call only), replica `replica` stops answering at its part in
+ * attempt from_attempt (counted from that call's first attempt): it publishes
+ * no pair message, reports nothing and leaves the launch at that step
+ * boundary, as a stalled or lost process would.  Its partner's bounded wait
+ * then runs out and the call returns RE_ETIMEOUT.  replica = -1 cancels.
+ * Nothing faults on the device: the replica only skips its messages. */
+int re_inject_stall(re_ctx *c, int replica, int from_attempt);
 
 /* One exchange attempt in every ensemble: the ladder sorted (by temperature;
  * by T/lam with potential scales), ladder positions (q, q + d) paired for

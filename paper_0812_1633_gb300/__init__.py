@@ -66,6 +66,8 @@ def lib():
         L.re_run_free.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int64),
                                   C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_uint8)]
+        L.re_set_wait_limit.argtypes = [vp, C.c_double]
+        L.re_inject_stall.argtypes = [vp, C.c_int, C.c_int]
         L.re_energies.argtypes = [vp, dp, dp, dp]
         L.re_temps.argtypes = [vp, dp]
         L.re_lambdas.argtypes = [vp, dp]
@@ -208,10 +210,24 @@ class Context:
         T = np.zeros(shape, np.float64)
         pa = np.zeros(shape, np.int32)
         ac = np.zeros(shape, np.uint8)
-        _check(lib().re_run_free(self._h, int(attempts), int(nx), _p(st, C.c_int64),
-                                 _p(T, C.c_double), _p(pa, C.c_int32), _p(ac, C.c_uint8)),
-               self._h)
+        code = lib().re_run_free(self._h, int(attempts), int(nx), _p(st, C.c_int64),
+                                 _p(T, C.c_double), _p(pa, C.c_int32), _p(ac, C.c_uint8))
+        try:
+            _check(code, self._h)
+        except REError as e:
+            if code == RE_ETIMEOUT:
+                e.log = (st, T, pa, ac)   # where every replica stopped
+            raise
         return st, T, pa, ac
+
+    def set_wait_limit(self, seconds):
+        """Limit (seconds) of the bounded device waits of run_free."""
+        _check(lib().re_set_wait_limit(self._h, float(seconds)), self._h)
+
+    def inject_stall(self, replica, from_attempt=0):
+        """Fault injection for the next run_free call: `replica` stops answering
+        at its part in attempt `from_attempt` of that call (-1 cancels)."""
+        _check(lib().re_inject_stall(self._h, int(replica), int(from_attempt)), self._h)
 
     def exchange(self, outputs=False):
         if not outputs:

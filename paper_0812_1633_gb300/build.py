@@ -1,6 +1,7 @@
 """Build the sm_103a shared library ``_build/libre_gb300.so`` with nvcc.
 
-Two translation units (kernels, C ABI) are compiled in parallel for
+The translation units (kernels, the batched kernel per precision and mode,
+the C ABI) are compiled in parallel for
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into one shared
 library with the CUDA runtime linked statically.  No cmake, no torch
 extension machinery: the library exposes a plain C ABI (``include/re.h``).
@@ -18,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libre_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["re_kernels.cu", "re_capi.cu", "re_noalloc.cu"]
+SOURCES = ["re_kernels.cu", "re_capi.cu", "re_noalloc.cu", "re_batched_f64.cu", "re_batched_mix.cu",
+           "re_batched_f64_async.cu", "re_batched_mix_async.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]

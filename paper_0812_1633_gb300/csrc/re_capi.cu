@@ -138,6 +138,9 @@ struct re_ctx {
   int32_t* d_log_acc = nullptr;
   int log_rows = 0;
   int resident_clusters = -1;  // batched clusters resident at once (-1: not yet queried)
+  double wait_s = 1.0;         // limit of the free-running exchange's bounded waits
+  int stall_rep = -1;          // fault injection for the next re_run_free (-1: none)
+  int stall_from = 0;
   // cached graph of re_run
   cudaGraphExec_t graph = nullptr;
   int graph_cycles = 0;
@@ -445,6 +448,21 @@ int32_t* out_status(re_ctx* c) { return reinterpret_cast<int32_t*>(out_U(c) + 3 
 int32_t* out_partner(re_ctx* c) { return out_status(c) + c->n_rep; }
 uint8_t* out_acc(re_ctx* c) { return reinterpret_cast<uint8_t*>(out_partner(c) + c->n_rep); }
 
+// RE_ETIMEOUT with message fmt(r).  A failed free-running launch leaves every
+// replica at a step boundary with a consistent state (a pair either swapped
+// on both sides or not at all), so the timeout marks are cleared on the
+// device once reported: the context goes on with the next call.
+int timeout_fail(re_ctx* c, const int32_t* st, const char* fmt, int r) {
+  const int code = fail(c, RE_ETIMEOUT, fmt, r);
+  std::vector<int32_t> cleared(st, st + c->n_rep);
+  for (auto& w : cleared) w &= ~(int32_t)(re::kStTimeout | re::kStAborted);
+  cudaError_t e = cudaMemcpyAsync(c->s.status, cleared.data(), sizeof(int32_t) * c->n_rep,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "clear timeout marks");
+  return code;
+}
+
 // The first error recorded in the replicas' status words.
 int status_eval(re_ctx* c, const int32_t* st) {
   for (int r = 0; r < c->n_rep; ++r) {
@@ -454,10 +472,16 @@ int status_eval(re_ctx* c, const int32_t* st) {
     if (st[r] & (re::kStNumeric | re::kStRngCap))
       return fail(c, RE_ENUMERIC, "replica %d: non-finite energy or thermostat draw", r);
   }
-  // a timed-out wait is reported after the errors that may have caused it
+  // a timed-out wait is reported after the errors that may have caused it;
+  // the replica whose own wait ran out is named before those it stopped
   for (int r = 0; r < c->n_rep; ++r)
     if (st[r] & re::kStTimeout)
-      return fail(c, RE_ETIMEOUT, "replica %d: free-running exchange wait gave up", r);
+      return timeout_fail(c, st, "replica %d: free-running exchange: its bounded wait ran out "
+                          "(or it stopped answering)", r);
+  for (int r = 0; r < c->n_rep; ++r)
+    if (st[r] & re::kStAborted)
+      return timeout_fail(c, st, "replica %d: free-running exchange stopped early by another "
+                          "replica's failed wait", r);
   return RE_OK;
 }
 
@@ -714,6 +738,13 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
     if (ce != cudaSuccess) rcode = cuda_fail(c, ce, "memset");
   }
   if (rcode == RE_OK) rcode = refresh(c);
+  // the group's first list build is a copy of lists the members had built
+  // and counted already: keep the members' rebuild counters
+  for (int i = 0; i < n && rcode == RE_OK; ++i) {
+    cudaError_t e = cudaMemcpyAsync(c->s.nreb + c->ens[i].rep_off, src[i]->s.nreb,
+                                    8 * (size_t)src[i]->n_rep, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) rcode = cuda_fail(c, e, "copy member counters");
+  }
   if (rcode == RE_OK) rcode = status_check(c);
   if (rcode != RE_OK) {
     g_create_error = c->err;
@@ -799,6 +830,10 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
   fr.n_att = n_att;
   fr.log_cap = want_log ? n_att : 0;
   fr.rtot = R;
+  fr.wait_ns = (uint64_t)(c->wait_s * 1e9);
+  fr.stall_rep = c->stall_rep;  // one call only
+  fr.stall_from = c->stall_from;
+  c->stall_rep = -1;
   fr.issue = c->d_fr_words;
   fr.abort_ = fr.issue + E;
   fr.partner = fr.abort_ + E;
@@ -814,12 +849,22 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
   fr.log_acc = c->d_log_acc;
   RE_CUDA(c, cudaMemsetAsync(c->d_fr_words, 0, sizeof(int32_t) * (2 * (size_t)E + 5 * (size_t)R),
                              c->stream), "clear exchange words");
+  if (want_log) {
+    // entries of replicas that never take part in an attempt keep step -1
+    const size_t n = (size_t)n_att * R;
+    RE_CUDA(c, cudaMemsetAsync(c->d_log_step, 0xFF, 8 * n, c->stream), "clear log");
+    RE_CUDA(c, cudaMemsetAsync(c->d_log_partner, 0xFF, 4 * n, c->stream), "clear log");
+    RE_CUDA(c, cudaMemsetAsync(c->d_log_acc, 0, 4 * n, c->stream), "clear log");
+    RE_CUDA(c, cudaMemsetAsync(c->d_log_T, 0, 8 * n, c->stream), "clear log");
+  }
   int rc = launch_advance(c, c->d_budget_nx, nullptr, n_att * nx, 0, &fr);
   if (rc) return rc;
   RE_CUDA(c, re::launch_attempt_add(c->s, E, n_att, c->stream), "attempt counters");
   if (!want_log) return RE_OK;
+  // the log is read back also when the launch failed: it shows where every
+  // replica stopped
   rc = status_check(c);
-  if (rc) return rc;
+  if (rc != RE_OK && rc != RE_ETIMEOUT) return rc;
   const size_t n = (size_t)n_att * R;
   if (log_step)
     RE_CUDA(c, cudaMemcpy(log_step, c->d_log_step, 8 * n, cudaMemcpyDeviceToHost), "read log");
@@ -832,6 +877,23 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
     RE_CUDA(c, cudaMemcpy(a.data(), c->d_log_acc, 4 * n, cudaMemcpyDeviceToHost), "read log");
     for (size_t k = 0; k < n; ++k) log_acc[k] = (uint8_t)a[k];
   }
+  return rc;
+}
+
+int re_set_wait_limit(re_ctx* c, double seconds) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (!(seconds >= 1e-4 && seconds <= 10.0))
+    return fail(c, RE_EINVAL, "wait limit must be in [1e-4, 10] seconds");
+  c->wait_s = seconds;
+  return RE_OK;
+}
+
+int re_inject_stall(re_ctx* c, int replica, int from_attempt) {
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (replica < -1 || replica >= c->n_rep || from_attempt < 0)
+    return fail(c, RE_EINVAL, "replica must be in [-1, n_rep) and from_attempt >= 0");
+  c->stall_rep = replica;
+  c->stall_from = from_attempt;
   return RE_OK;
 }
 

@@ -25,8 +25,11 @@ enum StatusBits : int {
   kStNumeric = 2,
   kStRngCap = 4,
   kStStop = 8,     // not an error: free-running stop request seen
-  kStTimeout = 16, // free-running exchange: a bounded wait ran out, or the launch ended early
-  kStXchg = 32     // not an error: an exchange pattern is waiting at this step boundary
+  kStTimeout = 16, // free-running exchange: this replica's own bounded wait ran out (or it
+                   // was told to stop answering: host-side fault injection)
+  kStXchg = 32,    // not an error: an exchange pattern is waiting at this step boundary
+  kStAborted = 64  // free-running exchange: left before the last pattern because another
+                   // replica of the ensemble gave up (raised the abort flag)
 };
 
 // Per-ensemble step constants, formed once on the host (FP64 transcendentals
@@ -114,6 +117,9 @@ struct FreeDev {
   int n_att;         // patterns per ensemble in this launch
   int log_cap;       // patterns logged (0: none)
   int rtot;          // replicas in the launch (log row stride)
+  uint64_t wait_ns;  // limit of every bounded wait (nanoseconds of the global timer)
+  int stall_rep;     // host-side fault injection: this replica (global index; -1: none)
+  int stall_from;    // stops answering at its part in pattern stall_from of the launch
   int32_t* issue;    // [E]
   int32_t* abort_;   // [E]
   int32_t* partner;  // [Rtot]
@@ -160,6 +166,18 @@ cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev*
 // Clusters of the batched kernel that can be resident at once with this
 // launch shape (0 when the query fails).
 int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int max_ncell);
+
+// One instantiation of the batched kernel (precision, threads per atom, list
+// placement, mode) and its launch; defined in re_batched.cuh, instantiated in
+// the re_batched_*.cu translation units.
+#define BATCHED_LAUNCH_ARGS                                                               \
+  const StateDev &s, const EnsDev *d_ens, const RepDev *d_rep, const int *d_work,        \
+      int n_work, const int32_t *d_budget, const LaunchCfg &cfg, int max_n, int max_ncell, \
+      size_t list_elems, int async_nx, cudaStream_t st, const FreeDev *fr
+template <bool FP64, int P, bool LSM, int MODE>
+cudaError_t launch_batched_t(BATCHED_LAUNCH_ARGS);
+template <bool FP64, int P, bool LSM>
+int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems);
 // applies externally decided exchange results, d_in = [T_new | lam_new |
 // vscale | uscale] (R values each, device)
 cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, cudaStream_t st);

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "re.h"
 #include "re_internal.h"
@@ -55,7 +56,9 @@ constexpr Layout layout() {
 }
 constexpr Layout kL = layout();
 
-void* g_scratch_dev[kMaxDevices];  // device address of g_scratch, per device
+// device address of g_scratch, per device; every thread that fills an entry
+// stores the same value, so relaxed atomic accesses suffice
+std::atomic<void*> g_scratch_dev[kMaxDevices];
 
 // errors are reported by return code only (a message would need allocation)
 int fail(int code, const char*) { return code; }
@@ -74,13 +77,13 @@ extern "C" int re_lj_forces_device_noalloc(int N, double L, double rc, int shift
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(RE_ECUDA, "no usable current device");
   // once per device, with that device current: the array's device address
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) return fail(RE_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
-    g_scratch_dev[dev] = p;
+  void* sp = g_scratch_dev[dev].load(std::memory_order_relaxed);
+  if (!sp) {
+    const cudaError_t e = cudaGetSymbolAddress(&sp, g_scratch);
+    if (e != cudaSuccess || !sp) return fail(RE_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+    g_scratch_dev[dev].store(sp, std::memory_order_relaxed);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_dev[dev]);
+  unsigned char* base = static_cast<unsigned char*>(sp);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   // the ensemble table of one replica (list radius rc + 0.5)

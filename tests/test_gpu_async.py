@@ -168,3 +168,65 @@ def test_free_running_refuses_non_resident_launch(re):
     ctx = re.Context(N, L, 2.5, inputs.geometric_ladder(0.7, 2.0, R), 1)
     with pytest.raises(re.REError):
         ctx.run_free(2, 5)
+
+
+def test_free_running_timeout_leaves_a_consistent_state(re):
+    """Failure detection of the free-running exchange (Implementation section:
+    the blocking pair receive becomes a bounded device wait).  Replica w stops
+    answering in attempt 3 of the launch (host-side fault injection: it sends
+    no pair message and leaves at that step boundary); its partner's wait runs
+    out after 5 ms, the call returns RE_ETIMEOUT, and every replica stops at
+    a step boundary.  Replayed on the FP64 oracle from the log: the earlier
+    attempts and the pairs of attempt 3 that completed take the oracle's
+    decisions, the pair of w swaps nothing, and the final x, v, T of every
+    replica equal the oracle's at the reported step counts.  The context then
+    goes on with ordinary calls.  (The replicas that are not waiting keep
+    stepping until the abort reaches them, a wait limit's worth of steps: the
+    limit is kept short so that the FP64 trajectories still agree to 1e-9.)"""
+    N, R, seed, nx, A, w, ks = 256, 8, 43, 10, 6, 3, 3
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, R)
+    ctx = re.Context(N, L, 2.5, temps, seed, precision="fp64")
+    ens = O.Ensemble(N, L, temps, seed)
+    ctx.set_wait_limit(0.005)
+    ctx.inject_stall(w, ks)
+    with pytest.raises(re.REError) as e:
+        ctx.run_free(A, nx, log=True)
+    assert e.value.code == re.RE_ETIMEOUT
+    steps, T, partner, acc = e.value.log
+    final, _ = ctx.counters()
+    prev = np.zeros(R, np.int64)
+    for k in range(ks):                       # complete attempts: as the replay test
+        assert (steps[k] >= 0).all()
+        ens.advance([int(x) for x in steps[k] - prev])
+        po, ao = ens.exchange()
+        assert np.array_equal(partner[k], po) and np.array_equal(acc[k].astype(bool), ao.astype(bool))
+        assert np.array_equal(T[k], ens.temps())
+        prev = steps[k].copy()
+    took = steps[ks] >= 0
+    assert not took[w] and final[w] >= prev[w]
+    # every other replica had seen the pattern before the abort
+    assert took.sum() == R - 1, steps[ks]
+    # to the step of its part in attempt ks (w: to where it stopped)
+    at = np.where(took, steps[ks], final)
+    ens.advance([int(x) for x in at - prev])
+    To, lo, po, ao, vs, us, _ = O.exchange_h(ens.temps(), ens.lams(), ens.energies(), seed, ks,
+                                             0, 1)
+    p = po[w]
+    assert p >= 0 and partner[ks, p] == w and acc[ks, p] == 0   # the stalled pair: no swap
+    for r in range(R):
+        if r in (w, p):
+            To[r], vs[r] = ens.reps[r].T, 1.0
+        else:
+            assert partner[ks, r] == po[r] and bool(acc[ks, r]) == bool(ao[r]), r
+    assert np.array_equal(np.sort(To), np.sort(temps))       # still a permutation
+    O.lib().orc_apply_exchange_h(ens._arr, R, O._dp(To), O._dp(lo), O._dp(vs), O._dp(us))
+    ens.advance([int(x) for x in final - at])
+    assert np.array_equal(ctx.temps(), ens.temps())
+    compare(ctx, ens, N, L, tol=1e-9)
+    # the context goes on: ordinary cycles, then a free-running launch
+    ctx.advance(10)
+    ctx.exchange()
+    ctx.run_free(2, nx)
+    assert np.isfinite(ctx.energies()[0]).all()
+    assert np.array_equal(np.sort(ctx.temps()), np.sort(temps))
