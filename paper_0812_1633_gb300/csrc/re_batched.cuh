@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
                                                              KernelDims dims, FreeDev fr) {
   constexpr int ND = (3 + P - 1) / P;  // coordinates per lane
   // replica constants live in shared memory, not in registers
-  __shared__ EnsDev E;
+  __shared__ EnsHdr E;
   __shared__ StepConst K;
   __shared__ double alpha_sh, kp_sh;
   __shared__ float eps_sh;
@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const int r = work[blockIdx.x / C];
   const RepDev rd = reps[r];
   if (threadIdx.x == 0) {
-    E = ens[rd.ens];
-    K = E.kc;
+    E = static_cast<const EnsHdr&>(ens[rd.ens]);
+    K = ens[rd.ens].kc;
     set_thermo_target(K, S.T[r]);
     set_potential_scale(K, S.lam[r]);
     Tcur_sh = S.T[r];
@@ -85,7 +85,15 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const int valid0 = S.valid[r];
   const double vs0 = S.vscale[r];
   const double fs0 = S.fscale[r];
-  double econs = S.econs[r];
+  // the replica's stored energies (U, K, econs), kept by thread 0 of each CTA
+  // in shared memory (CTA 0's are written back); registers are kept for the
+  // per-atom state
+  __shared__ double U_sh, K_sh, econs_sh;
+  if (threadIdx.x == 0) {
+    U_sh = S.U[r];
+    K_sh = S.K[r];
+    econs_sh = S.econs[r];
+  }
   const int64_t step0 = S.step[r];
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -128,12 +136,20 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const float ucf = (float)K.uc;
   const bool thermo = E.tau > 0.0;  // decided once; no FP64 tests inside the step loop
 
-  // per-lane state in registers
+  // per-lane state in registers (the FP32 velocity of the mixed path is
+  // formed from the fixed-point word when needed, and the positions at the
+  // last list build are kept in shared memory: registers are the scarce
+  // resource of this kernel, which holds the state for a whole launch)
   uint64_t xq[ND];
   double v[ND], f[ND];       // FP64 path
   long long vq[ND];          // mixed path: velocity, fixed point
-  float vf[ND], hf[ND];      // mixed path: FP32 velocity copy, half-kick increment
-  uint32_t ref[ND];
+  float hf[ND];              // mixed path: half-kick increment
+  // top 32 bits of the coordinates at the last list build: in shared memory
+  // on the mixed path (3 words per own atom), in registers on the FP64 path
+  // (whose shared memory holds 64-bit positions)
+  uint32_t ref_r[ND];
+  uint32_t* ref_sm = FP64 ? nullptr : sm.ref + (size_t)(i - i0) * 3;
+  auto ref = [&](int j) -> uint32_t& { return FP64 ? ref_r[j] : ref_sm[q + j * P]; };
   int cnt = 0;
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
@@ -141,23 +157,24 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     xq[j] = 0;
     v[j] = f[j] = 0.0;
     vq[j] = 0;
-    vf[j] = hf[j] = 0.0f;
-    ref[j] = 0;
+    hf[j] = 0.0f;
+    ref_r[j] = 0;
     if (own && d < 3) {
       xq[j] = qcomp(S, d)[g];
       const double vv = vcomp(S, d)[g] * vs0;
       const double ff = fcomp(S, d)[g] * fs0;
-      ref[j] = rcomp(S, d)[g];
+      ref(j) = rcomp(S, d)[g];
       if (FP64) {
         v[j] = vv;
         f[j] = ff;
       } else {
         vq[j] = __double2ll_rn(vv * 0x1.0p48);  // once per launch
-        vf[j] = (float)vv;
         hf[j] = (float)(ff * K.hdt);
       }
     }
   }
+  // FP32 copy of velocity word j (mixed path)
+  auto vf = [&](int j) { return ll2f_split(vq[j]) * kVelUnit; };
   if (own) cnt = ncnt[(size_t)i * P + q];
 
   auto hi_of = [&](int a) -> Hi3 {
@@ -169,8 +186,20 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       return Hi3{p.x, p.y, p.z};
     }
   };
-  // broadcast this lane's coordinates of atom i to every CTA of the cluster
+  // broadcast this lane's coordinates of atom i to every CTA of the cluster.
+  // Mixed path: the top 32 bits of each coordinate, and in .w the next 10 bits
+  // of x, y, z (bits 20-29, 10-19, 0-9), gathered from the atom's lanes by
+  // lane q == 0, for the exact cutoff test of mixed_pair.
   auto publish = [&]() {
+    uint32_t low = 0;
+    if (!FP64) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const uint32_t b = __shfl_sync(0xffffffffu, (uint32_t)(xq[d / P] >> 22) & 1023u,
+                                       (lane & ~(P - 1)) | (d % P));
+        low |= b << (20 - 10 * d);
+      }
+    }
     if (!own) return;
 #pragma unroll
     for (int j = 0; j < ND; ++j) {
@@ -184,6 +213,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         const uint32_t hv = (uint32_t)(xq[j] >> 32);
         for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(dst, rk) = hv;
       }
+    }
+    if (!FP64 && q == 0) {
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&posm[i]) + 3;
+      for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(dst, rk) = low;
     }
   };
 
@@ -231,7 +264,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     }
     if (own) {
 #pragma unroll
-      for (int j = 0; j < ND; ++j) ref[j] = (uint32_t)(xq[j] >> 32);
+      for (int j = 0; j < ND; ++j)
+        if (q + j * P < 3) ref(j) = (uint32_t)(xq[j] >> 32);
     }
     ++nreb;
   };
@@ -266,12 +300,12 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       du = warp_sum(du);
       dk = warp_sum(dk);
     } else {
-      MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
+      MixedAcc a{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0};
       if (own) {
         if (energy)
-          a = mixed_sublist_forces<true>(posm[i], posm, nb, mycol, ncols, cnt, K.rc2u, K.inv_lam2);
+          a = mixed_sublist_forces<true>(i, posm, nb, mycol, ncols, cnt, K);
         else
-          a = mixed_sublist_forces<false>(posm[i], posm, nb, mycol, ncols, cnt, K.rc2u, K.inv_lam2);
+          a = mixed_sublist_forces<false>(i, posm, nb, mycol, ncols, cnt, K);
       }
       const float ax = group_sum<P>(a.fx), ay = group_sum<P>(a.fy), az = group_sum<P>(a.fz);
       float ae = 0.0f;
@@ -288,7 +322,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           const int d = q + j * P;
           if (d >= 3) continue;
           hf[j] = (d == 0 ? ax : (d == 1 ? ay : az)) * K.hlf;
-          const float w = kick ? vf[j] + hf[j] : vf[j];
+          const float w = kick ? vf(j) + hf[j] : vf(j);
           kl = fmaf(w, w, kl);
         }
         if (!isfinite(kl)) st |= kStNumeric;
@@ -353,7 +387,6 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     __syncthreads();
   }
 
-  double U = S.U[r], Kin = S.K[r];
   int status = 0;
 
   if (!valid0) {
@@ -366,14 +399,19 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     if (FP64) {
       double su, sk;
       totals_fp64(su, sk, status);
-      U = 0.5 * su * K.lamv;
-      Kin = 0.5 * sk;
-      if (!isfinite(U) || !isfinite(Kin)) status |= kStNumeric;
+      const double U0 = 0.5 * su * K.lamv, K0 = 0.5 * sk;
+      if (!isfinite(U0) || !isfinite(K0)) status |= kStNumeric;
+      if (tid == 0) {
+        U_sh = U0;
+        K_sh = K0;
+      }
     } else {
       long long iu, ik;
       totals_int(iu, ik, status, true);
-      U = 0.5 * (double)iu * kEnUnit * K.lamv;  // FP64 only for the stored energies
-      Kin = 0.5 * (double)ik * kEnUnit;
+      if (tid == 0) {
+        U_sh = 0.5 * (double)iu * kEnUnit * K.lamv;  // FP64 only for the stored energies
+        K_sh = 0.5 * (double)ik * kEnUnit;
+      }
     }
   }
 
@@ -409,13 +447,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           if (first_kick) v[j] += K.hdt * f[j];
           xq[j] += (uint64_t)__double2ll_rn(v[j] * K.dtq);
         } else {
-          if (first_kick) {
-            vq[j] += f2ll_split(hf[j] * kVelScale);
-            vf[j] = ll2f_split(vq[j]) * kVelUnit;
-          }
-          xq[j] += (uint64_t)f2ll_split(vf[j] * dtqf);
+          if (first_kick) vq[j] += f2ll_split(hf[j] * kVelScale);
+          xq[j] += (uint64_t)f2ll_split(vf(j) * dtqf);
         }
-        const float dd = (float)(int)((uint32_t)(xq[j] >> 32) - ref[j]);
+        const float dd = (float)(int)((uint32_t)(xq[j] >> 32) - ref(j));
         d2 = fmaf(dd, dd, d2);
       }
     }
@@ -492,9 +527,11 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           if (!bnd) v[j] += K.hdt * f[j];  // first half kick of the next step
         }
       }
-      U = Un;
-      Kin = Kp;
-      econs += Kn - Kp;
+      if (tid == 0) {
+        U_sh = Un;
+        K_sh = Kp;
+        econs_sh += Kn - Kp;
+      }
     } else {
       // warp 0 forms the integer totals and alpha - 1 (FP32); the block reads
       // them after a block barrier (far cheaper than every warp repeating it)
@@ -519,11 +556,10 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         for (int j = 0; j < ND; ++j) {
           const int d = q + j * P;
           if (d >= 3) continue;
-          const float w = vf[j] + hf[j];
+          const float w = vf(j) + hf[j];
           // second half kick + thermostat factor (+ next first half kick)
           const float inc = fmaf(eps, w, bnd ? hf[j] : 2.0f * hf[j]);
           vq[j] += f2ll_split(inc * kVelScale);
-          vf[j] = ll2f_split(vq[j]) * kVelUnit;
         }
       }
       // FP64 bookkeeping of the stored energies, off the step's critical path:
@@ -545,10 +581,13 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
             dsum += Kn - Kn * a1 * a1;
             if (t == slot) kp = Kn * a1 * a1;
           }
-          econs += warp_sum(dsum);
+          dsum = warp_sum(dsum);
           kp = __shfl_sync(0xffffffffu, kp, (slot - fold0) & 31);
-          Kin = kp;
-          if (energy) U = 0.5 * (double)iu * kEnUnit * K.lamv;
+          if (lane == 0) {
+            econs_sh += dsum;
+            K_sh = kp;
+            if (energy) U_sh = 0.5 * (double)iu * kEnUnit * K.lamv;
+          }
           __syncwarp();
           if (lane == 0) fold0_sh = slot + 1 == kNoiseChunk ? 0 : slot + 1;
           __syncwarp();
@@ -577,7 +616,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         int pid, acc;
         bool ok;
         const double sc = pair_exchange(fr, S, E, rd, r, k_next, A0_sh + k_next, Tcur_sh, K.lamv,
-                                        U, &Tn, &ln, &us, &pid, &acc, &ok);
+                                        U_sh, &Tn, &ln, &us, &pid, &acc, &ok);
         if (k_next < fr.log_cap) {
           const size_t li = (size_t)k_next * fr.rtot + r;
           fr.log_step[li] = step0 + done;
@@ -608,7 +647,6 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
             v[j] *= sc;
           } else {
             vq[j] = __double2ll_rn((double)vq[j] * sc);
-            vf[j] = ll2f_split(vq[j]) * kVelUnit;
           }
         }
       }
@@ -620,12 +658,14 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
           else hf[j] *= (float)us;
         }
       }
-      const double Ks = Kin * (sc * sc);
-      econs += Kin - Ks;
-      Kin = Ks;
-      const double Us = U * us;
-      econs += U - Us;
-      U = Us;
+      if (tid == 0) {
+        const double Ks = K_sh * (sc * sc);
+        econs_sh += K_sh - Ks;
+        K_sh = Ks;
+        const double Us = U_sh * us;
+        econs_sh += U_sh - Us;
+        U_sh = Us;
+      }
       // read by the other threads only after the next barriers; the lam
       // comparison reads K before thread 0 may change it
       const bool new_lam = ln != K.lamv;
@@ -672,7 +712,7 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
       const int d = q + j * P;
       if (d >= 3) continue;
       qcomp(S, d)[g] = xq[j];
-      rcomp(S, d)[g] = ref[j];
+      rcomp(S, d)[g] = ref(j);
       if (FP64) {
         vcomp(S, d)[g] = v[j];
         fcomp(S, d)[g] = f[j];
@@ -684,9 +724,9 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     ncnt[(size_t)i * P + q] = cnt;
   }
   if (crank == 0 && tid == 0) {
-    S.U[r] = U;
-    S.K[r] = Kin;
-    S.econs[r] = econs;
+    S.U[r] = U_sh;
+    S.K[r] = K_sh;
+    S.econs[r] = econs_sh;
     S.step[r] = step0 + done;
     S.nreb[r] += nreb;
     S.vscale[r] = 1.0;
@@ -707,7 +747,11 @@ cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDe
                                    const FreeDev* fr) {
   const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
   auto fn = md_batched_kernel<FP64, P, LSM, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  if (fa.sharedSizeBytes > kBatchedStaticSmem) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // the rest of the SM's 256 KB serves as L1 (lists in global memory, state)
   int per_sm = 0;
@@ -731,7 +775,9 @@ cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDe
   KernelDims dims{max_n, max_ncell, list_elems, async_nx};
   FreeDev f{};
   if (fr) f = *fr;
-  return cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims, f);
+  e = cudaLaunchKernelEx(&lc, fn, s, d_ens, d_rep, d_work, d_budget, dims, f);
+  if (e != cudaSuccess) cudaGetLastError();  // a refused launch leaves no error behind
+  return e;
 }
 
 template <bool FP64, int P, bool LSM>

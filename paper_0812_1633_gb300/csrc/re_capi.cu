@@ -201,6 +201,10 @@ void finish_ens(EnsDev& e) {
   k.rc2 = e.rc * e.rc;
   const double rcu = e.rc / k.lam32;
   k.rc2u = (float)(rcu * rcu);
+  k.rc2u_lo = (float)(rcu * rcu * (1.0 - 2e-6));
+  k.rc2u_hi = (float)(rcu * rcu * (1.0 + 2e-6));
+  const double rcx = e.rc / (e.L * 0x1.0p-42);
+  k.rc2x = rcx * rcx;
   // list radius rounded up, half skin rounded down: the list never misses a pair
   const double rlu = e.rlist * (1.0 + 1e-6) / k.lam32;
   k.rl2u = (float)(rlu * rlu);
@@ -370,7 +374,7 @@ size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
   }
   const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
                                              c->opt.precision == RE_PREC_FP64, elems);
-  return smem <= (size_t)max_smem_optin() ? elems : 0;
+  return smem + re::kBatchedStaticSmem <= (size_t)max_smem_optin() ? elems : 0;
 }
 
 int check_cfg(re_ctx* c, const LaunchCfg& k) {
@@ -382,7 +386,8 @@ int check_cfg(re_ctx* c, const LaunchCfg& k) {
     return fail(c, RE_EINVAL, "%d atoms per CTA x %d threads per atom exceed 1024 threads; "
                 "use more CTAs per replica", (c->max_n + k.cluster - 1) / k.cluster, k.atom_threads);
   const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
-                                             c->opt.precision == RE_PREC_FP64, 0);
+                                             c->opt.precision == RE_PREC_FP64, 0) +
+                      re::kBatchedStaticSmem;
   const int maxsm = max_smem_optin();
   if (smem > (size_t)maxsm)
     return fail(c, RE_EINVAL, "replica of %d atoms needs %zu bytes of shared memory (max %d)",

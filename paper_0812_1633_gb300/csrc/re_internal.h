@@ -40,15 +40,17 @@ struct StepConst {
   double lam32, lam64, inv_l, dtq, hdt, inv_hdt, uc, rc2, c_th, kbar;
   double kbar1, af1, bf1, gf1;  // kbar = kbar1 T, af = af1 T, bf = bf1 sqrt(T), gf = gf1 / sqrt(T)
   double lamv;                  // the replica's potential scale (set_potential_scale)
+  double rc2x;                  // rc^2 in units (L / 2^42)^2 (exact cutoff test, mixed path)
   float hlf;                    // FP32 half-kick factor per force unit, times lamv
   float rc2u, rl2u, half2u, inv_lam2;
+  float rc2u_lo, rc2u_hi;       // rc2u (1 -+ 2e-6): the band decided on 42-bit separations
   // thermostat constants of the mixed path (used in FP32): c - 1,
   // (1 - c) Kbar / Nf, 2 sqrt(c (1 - c) Kbar / Nf), sqrt(c Nf / ((1 - c) Kbar))
   float cm1f, af, bf, gf;
   int nf, pad_;
 };
 
-struct EnsDev {
+struct EnsHdr {
   int N, R, rep_off, pair_off;  // replicas [rep_off, rep_off + R); stats at pair_off
   int nc, m;                    // list cells per side (0: all pairs), reach in cells
   int cap;                      // neighbour entries per atom: max over P of P * capsub[P]
@@ -56,6 +58,12 @@ struct EnsDev {
   int shift, parity_mode, xdist;  // xdist: exchange pairs at ladder distance xdist (>= 1)
   double L, rc, rlist, skin, dt, tau;
   uint64_t seed;
+};
+
+// An ensemble: its parameters and the step constants derived from them (the
+// batched kernel keeps the two apart in shared memory, the constants per
+// replica).
+struct EnsDev : EnsHdr {
   StepConst kc;  // filled by finish_ens (host) once the fields above are set
 };
 
@@ -151,6 +159,9 @@ void finish_ens(EnsDev& e);
 cudaError_t launch_init_lattice(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                 int n_rep, int max_threads, cudaStream_t st);
 size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size_t list_elems);
+// Shared memory the batched kernel declares statically (replica constants and
+// hand-over words), reserved on top of batched_smem_bytes; launches check it.
+constexpr size_t kBatchedStaticSmem = 512;
 // list_elems > 0: each CTA keeps its atoms' neighbour sub-lists (list_elems
 // uint16 entries) in shared memory during the launch
 // async_nx > 0: master-stop mode (budgets ignored): in every ensemble the

@@ -118,13 +118,67 @@ __device__ __forceinline__ float sep2_hi(Hi3 a, Hi3 b) {
 // and energy are FP32; the per-atom sums are FP32 over this atom's list and
 // are folded into FP64 by the caller.  Force on i from j = fs * d with
 // fs = s^4 (24 - 48 s^3), s = 1/r^2 (sigma units); pair energy 4 s^3 (s^3 - 1).
+//
+// The cutoff test.  The force is truncated at rc (Example section), so it
+// jumps there by F(rc) ~ 0.04: a pair put on the wrong side of rc costs its
+// atoms a force error of ~1e-3 of the rms force, and the FP32 r^2 (relative
+// error below 3e-7) would do that for pairs within ~1e-7 of rc -- about one
+// pair per ten evaluations of a 4000-atom replica.  So FP32 decides every
+// pair outside a relative band of 2e-6 around rc^2, and pairs inside the band
+// are decided in FP64 on 42-bit separations: the top 32 bits and the next 10
+// bits of each coordinate (kept in .w of the shared-memory position, 10 bits
+// per coordinate).  The result equals the FP64 test on the full positions
+// except for pairs within ~1e-11 of rc.
 struct MixedAcc {
   float fx, fy, fz, e;
   int nin;
+  float r2max;  // largest r^2 counted inside ...
+  int jmax;     // ... and its atom (checked exactly when r2max lies in the band)
 };
 
+// The cutoff constants the pair loop keeps in registers; the band's lower
+// edge and rc^2 in 42-bit units are read from the step constants (shared
+// memory) only after the loop, so that they hold no register during it.
+struct MixedCut {
+  float hi;         // rc^2 (1 + 2e-6), units (L / 2^32)^2
+  float inv_lam2;   // (2^32 / L)^2
+};
+
+// 42-bit minimum-image separation of one coordinate: top 32 bits (hj, hi) and
+// the next 10 bits (lj, li) of the two positions.
+__device__ __forceinline__ double sep42(uint32_t hj, uint32_t hi, uint32_t lj, uint32_t li) {
+  return (double)(((long long)(int)(hj - hi) << 10) + ((long long)lj - (long long)li));
+}
+
+__device__ __forceinline__ bool inside_cutoff_42(uint4 pi, uint4 pj, double x42) {
+  const double dx = sep42(pj.x, pi.x, (pj.w >> 20) & 1023u, (pi.w >> 20) & 1023u);
+  const double dy = sep42(pj.y, pi.y, (pj.w >> 10) & 1023u, (pi.w >> 10) & 1023u);
+  const double dz = sep42(pj.z, pi.z, pj.w & 1023u, pi.w & 1023u);
+  return fma(dx, dx, fma(dy, dy, dz * dz)) < x42;
+}
+
+// The pair force on i from j: fs * d with fs = s^4 (24 - 48 s^3), s = 1/r^2
+// (sigma units), d = (dx, dy, dz); energy 4 s^3 (s^3 - 1).
+template <bool ENERGY>
+__device__ __forceinline__ void mixed_pair_add(float r2, float dx, float dy, float dz,
+                                               float inv_lam2, float sign, MixedAcc& a) {
+  const float s = rcp_approx(r2) * inv_lam2;
+  const float s3 = s * s * s;
+  const float fs = sign * (s * s3) * fmaf(-48.0f, s3, 24.0f);
+  a.fx = fmaf(fs, dx, a.fx);
+  a.fy = fmaf(fs, dy, a.fy);
+  a.fz = fmaf(fs, dz, a.fz);
+  if (ENERGY) {
+    a.e = fmaf(sign * s3, fmaf(4.0f, s3, -4.0f), a.e);
+    a.nin += (int)sign;
+  }
+}
+
+// Every pair with FP32 r^2 < cut.hi is counted inside; a.r2max and a.jmax
+// remember the largest such r^2 and its atom.  The caller then checks that
+// pair exactly when it lies in the band (mixed_cut_fix).
 template <bool ENERGY, bool MAYBE_SELF>
-__device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, float rc2u, float inv_lam2,
+__device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, int j, const MixedCut& cut,
                                            MixedAcc& a) {
   const float dx = (float)(int)(pj.x - pi.x);
   const float dy = (float)(int)(pj.y - pi.y);
@@ -132,16 +186,29 @@ __device__ __forceinline__ void mixed_pair(uint4 pi, uint4 pj, float rc2u, float
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   // r2 == 0 only for the atom itself (sub-list padding, last block only);
   // distinct atoms at distance 0 are reported by the list build
-  if (r2 < rc2u && (!MAYBE_SELF || r2 > 0.0f)) {
-    const float s = rcp_approx(r2) * inv_lam2;
-    const float s3 = s * s * s;
-    const float fs = (s * s3) * fmaf(-48.0f, s3, 24.0f);
-    a.fx = fmaf(fs, dx, a.fx);
-    a.fy = fmaf(fs, dy, a.fy);
-    a.fz = fmaf(fs, dz, a.fz);
-    if (ENERGY) {
-      a.e = fmaf(s3, fmaf(4.0f, s3, -4.0f), a.e);
-      a.nin += 1;
+  if (r2 < cut.hi && (!MAYBE_SELF || r2 > 0.0f)) {
+    if (r2 > a.r2max) {
+      a.r2max = r2;
+      a.jmax = j;
+    }
+    mixed_pair_add<ENERGY>(r2, dx, dy, dz, cut.inv_lam2, 1.0f, a);
+  }
+}
+
+// After the sub-list: if the largest r^2 counted lies in the band and the
+// 42-bit separations put that pair outside rc, take its contribution out
+// again.  (A second band pair in one sub-list -- about one sub-list in 1e8 --
+// stays counted as the FP32 test decided.)
+template <bool ENERGY>
+__device__ __forceinline__ void mixed_cut_fix(const uint4* pos, int i, const StepConst& K,
+                                              MixedAcc& a) {
+  if (a.r2max > K.rc2u_lo) {
+    const uint4 pi = pos[i], pj = pos[a.jmax];
+    if (!inside_cutoff_42(pi, pj, K.rc2x)) {
+      const float dx = (float)(int)(pj.x - pi.x);
+      const float dy = (float)(int)(pj.y - pi.y);
+      const float dz = (float)(int)(pj.z - pi.z);
+      mixed_pair_add<ENERGY>(a.r2max, dx, dy, dz, K.inv_lam2, -1.0f, a);
     }
   }
 }
@@ -161,6 +228,7 @@ struct BatchedSmem {
   int* wscan;      // 2 x (threads + 1): block scan of own atoms in cell order
   uint16_t* own_sorted;  // threads: sorted slots of this CTA's atoms
   int* cnt_sh;     // threads: sub-list counts handed to the owners
+  uint32_t* ref;     // 3 per own atom: top 32 bits of the coordinates at the last list build
   long long* rec_k;  // kNoiseChunk: 2K of each step (fixed point), CTA 0
   float* rec_e;      // kNoiseChunk: alpha - 1 of each step
   uint16_t* acell;
@@ -191,6 +259,7 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
   const size_t o_md = take((size_t)kMaxCluster * kMaxWarps * 4, 4);
   const size_t o_st = take(kMaxCluster * 4, 4);
   const size_t o_isc = take(64 * 4, 4);
+  const size_t o_ref = take(fp64 ? 0 : (size_t)threads * 3 * 4, 4);  // own atoms <= threads
   const size_t o_rk = take((size_t)kNoiseChunk * 8, 8);
   const size_t o_re = take((size_t)kNoiseChunk * 4, 4);
   const size_t o_cs = take((size_t)(max_ncell + 1) * 4, 4);
@@ -211,6 +280,7 @@ __host__ __device__ inline size_t batched_layout(int max_n, int max_ncell, int t
     out->slot_md = reinterpret_cast<float*>(base + o_md);
     out->slot_st = reinterpret_cast<int*>(base + o_st);
     out->iscr = reinterpret_cast<int*>(base + o_isc);
+    out->ref = reinterpret_cast<uint32_t*>(base + o_ref);
     out->rec_k = reinterpret_cast<long long*>(base + o_rk);
     out->rec_e = reinterpret_cast<float*>(base + o_re);
     out->cstart = reinterpret_cast<int*>(base + o_cs);
@@ -331,11 +401,13 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
 // only the last block can hold padding, so only it tests for the atom itself.
 // ENERGY: also sum the pair energies (needed only when U is reported).
 template <bool ENERGY>
-__device__ __forceinline__ MixedAcc mixed_sublist_forces(uint4 pi, const uint4* __restrict__ pos,
+__device__ __forceinline__ MixedAcc mixed_sublist_forces(int i, const uint4* __restrict__ pos,
                                                          const uint16_t* __restrict__ nb,
                                                          uint32_t col, uint32_t ncols, int cnt,
-                                                         float rc2u, float inv_lam2) {
-  MixedAcc a{0.f, 0.f, 0.f, 0.f, 0};
+                                                         const StepConst& K) {
+  MixedAcc a{0.f, 0.f, 0.f, 0.f, 0, 0.f, 0};
+  const MixedCut cut{K.rc2u_hi, K.inv_lam2};
+  const uint4 pi = pos[i];
   const size_t stride4 = (size_t)ncols * 4;
   const uint16_t* base = nb + (size_t)col * 4;
   const int nblk = (cnt + 3) >> 2;
@@ -344,26 +416,29 @@ __device__ __forceinline__ MixedAcc mixed_sublist_forces(uint4 pi, const uint4* 
   for (int kb = 0; kb < nfull; ++kb) {
     // the next block of indices is requested before this block is used
     const uint2 wn = kb + 1 < nblk ? *reinterpret_cast<const uint2*>(base + (size_t)(kb + 1) * stride4) : w;
-    const uint4 p0 = pos[w.x & 0xFFFFu];
-    const uint4 p1 = pos[w.x >> 16];
-    const uint4 p2 = pos[w.y & 0xFFFFu];
-    const uint4 p3 = pos[w.y >> 16];
-    mixed_pair<ENERGY, false>(pi, p0, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, false>(pi, p1, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, false>(pi, p2, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, false>(pi, p3, rc2u, inv_lam2, a);
+    const int j0 = w.x & 0xFFFFu, j1 = w.x >> 16, j2 = w.y & 0xFFFFu, j3 = w.y >> 16;
+    const uint4 p0 = pos[j0];
+    const uint4 p1 = pos[j1];
+    const uint4 p2 = pos[j2];
+    const uint4 p3 = pos[j3];
+    mixed_pair<ENERGY, false>(pi, p0, j0, cut, a);
+    mixed_pair<ENERGY, false>(pi, p1, j1, cut, a);
+    mixed_pair<ENERGY, false>(pi, p2, j2, cut, a);
+    mixed_pair<ENERGY, false>(pi, p3, j3, cut, a);
     w = wn;
   }
   if (nblk > nfull) {
-    const uint4 p0 = pos[w.x & 0xFFFFu];
-    const uint4 p1 = pos[w.x >> 16];
-    const uint4 p2 = pos[w.y & 0xFFFFu];
-    const uint4 p3 = pos[w.y >> 16];
-    mixed_pair<ENERGY, true>(pi, p0, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, true>(pi, p1, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, true>(pi, p2, rc2u, inv_lam2, a);
-    mixed_pair<ENERGY, true>(pi, p3, rc2u, inv_lam2, a);
+    const int j0 = w.x & 0xFFFFu, j1 = w.x >> 16, j2 = w.y & 0xFFFFu, j3 = w.y >> 16;
+    const uint4 p0 = pos[j0];
+    const uint4 p1 = pos[j1];
+    const uint4 p2 = pos[j2];
+    const uint4 p3 = pos[j3];
+    mixed_pair<ENERGY, true>(pi, p0, j0, cut, a);
+    mixed_pair<ENERGY, true>(pi, p1, j1, cut, a);
+    mixed_pair<ENERGY, true>(pi, p2, j2, cut, a);
+    mixed_pair<ENERGY, true>(pi, p3, j3, cut, a);
   }
+  mixed_cut_fix<ENERGY>(pos, i, K, a);
   return a;
 }
 
@@ -536,7 +611,7 @@ __device__ bool wait_at_least(const int* p, int want, const int* abort_flag, uin
 
 // The master's part, by one warp: pattern k of ensemble e.  Returns false when
 // a wait gave up.
-__device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsDev& E, int e, int k,
+__device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsHdr& E, int e, int k,
                               int64_t attempt) {
   const int lane = threadIdx.x & 31;
   const int R = E.R, base = E.rep_off;
@@ -580,7 +655,7 @@ __device__ bool issue_pattern(const FreeDev& fr, const StateDev& S, const EnsDev
 // Returns the velocity scale sqrt(T_new / T_old) and sets *us =
 // lam_new / lam_old (both 1 when not accepted); *ok = false when the wait
 // gave up.
-__device__ double pair_exchange(const FreeDev& fr, const StateDev& S, const EnsDev& E,
+__device__ double pair_exchange(const FreeDev& fr, const StateDev& S, const EnsHdr& E,
                                 const RepDev& rd, int r, int k, int64_t attempt, double Tcur,
                                 double lcur, double U, double* Tnew, double* lnew, double* us,
                                 int* partner_out, int* acc_out, bool* ok) {
