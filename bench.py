@@ -328,7 +328,7 @@ def run_gpu(args, cfg):
     if args.launch:
         cl, at, cd = (int(v) for v in args.launch.split(","))
         ctx.close()
-        ctx = make(skin, cluster=cl, atom_threads=at, cell_div=cd)
+        ctx = make(skin, cluster=cl, atom_threads=at, cell_div=cd, wide_launch=args.wide)
         tuned = ctx.config()
     elif skin_trials is None:
         tuned = ctx.autotune(steps=40)
@@ -514,7 +514,9 @@ def run_gpu(args, cfg):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "async": free,
             "graph": graph,
-            "gpu_launches": 2 * K,
+            # per step: the advance (one launch, or the ranking kernel and the
+            # two classes of a split launch) and the exchange
+            "gpu_launches": (4 if tuned.get("wide_n") else 2) * K,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -872,6 +874,8 @@ def main():
     ap.add_argument("--drift-r", type=int, default=8)
     ap.add_argument("--drift-steps", type=int, default=20000)
     ap.add_argument("--drift-window", type=int, default=4000)
+    ap.add_argument("--wide", type=int, default=0,
+                    help="with --launch: split launch 1 (where it applies), -1 never, 0 default")
     ap.add_argument("--launch", default=None,
                     help="fixed launch shape 'cluster,atom_threads,cell_div' instead of the autotuner")
     args = ap.parse_args()

@@ -77,7 +77,7 @@ typedef struct re_opts {
   int nx;           /* steps per replica used by re_advance(c, NULL); default 10      */
   int nbr_capacity; /* neighbours per atom; 0: from the density with a 6-sigma margin */
   int cell_div;     /* list cells per list radius (1..3); 0: automatic               */
-  int cluster;      /* CTAs cooperating on one replica (1, 2, 4, 8); 0: automatic     */
+  int cluster;      /* CTAs cooperating on one replica (1, 2, 3, 4, 8); 0: automatic  */
   int atom_threads; /* threads sharing one atom's neighbour list (1, 2, 4, 8); 0: auto */
   int sort_interval;/* mixed batched path: renumber each replica's atoms in space order
                        every this many steps (0: every 200; < 0: never).  Results
@@ -96,6 +96,16 @@ typedef struct re_opts {
                        they fit (copied in and out at every launch, so they pay off only
                        for long launches); -1: global memory, also for re_autotune.
                        re_autotune tries both unless this is 1 or -1. */
+  int wide_launch;  /* split launch of a one-ensemble batched context (budget mode):
+                       when the uniform launch leaves SMs idle, the hottest replicas
+                       (by current temperature; they rebuild their lists most often)
+                       run concurrently with one more CTA each, filling those SMs.
+                       0 (default): one launch, and re_autotune times the split
+                       against it; 1: always where it applies; -1: never.
+                       The wide replicas take clusters of twice the CTAs with the
+                       same threads per atom (re_config_wide), so the trajectories do
+                       not change: the mixed path's sums are exact integers, and the
+                       FP64 path differs only in the summation order of its energies. */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -266,9 +276,15 @@ int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *a
 /* re_config and whether the neighbour lists are kept in shared memory. */
 int re_config_ex(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads,
                  int *lists_smem);
-/* Times candidate launch configurations (cluster, atom_threads, cell_div and
- * the lists' placement, global or shared memory) over `steps` steps each on a
- * copy of the state and keeps the fastest; the state is restored afterwards. */
+/* The split launch in use (re_opts.wide_launch): replicas in the wide class,
+ * CTAs per wide replica, threads per wide CTA, threads per atom in the wide
+ * class (all 0: one launch).  Any pointer may be NULL. */
+int re_config_wide(const re_ctx *c, int *wide_n, int *wide_cluster, int *wide_threads,
+                   int *wide_atom_threads);
+/* Times candidate launch configurations (cluster, atom_threads, cell_div,
+ * the lists' placement, global or shared memory, and each as one launch or
+ * split, see re_opts.wide_launch) over `steps` steps each on a copy of the
+ * state and keeps the fastest; the state is restored afterwards. */
 int re_autotune(re_ctx *c, int steps);
 /* Queues subsequent work on stream (a cudaStream_t; NULL: legacy default). */
 int re_set_stream(re_ctx *c, void *stream);

@@ -109,6 +109,9 @@ struct re_ctx {
   EnsDev* d_ens = nullptr;
   RepDev* d_rep = nullptr;
   int* d_work = nullptr;
+  int* d_work2 = nullptr;           // split launch: work lists of the two classes
+  cudaStream_t side = nullptr;      // split launch: the wide class runs here
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* d_budget = nullptr;      // n_rep, per call
   int32_t* d_budget_nx = nullptr;   // n_rep, filled with opt.nx
   int32_t* d_budget_run = nullptr;  // n_cycles * n_rep for re_run
@@ -248,6 +251,39 @@ int sm_count() {
   return n > 0 ? n : 148;
 }
 
+// The split launch of shape k (see LaunchCfg): for a one-ensemble batched
+// context whose uniform launch leaves SMs idle, the hottest replicas get
+// clusters of twice the CTAs (cluster sizes that pair up on the GPU like the
+// uniform ones), as many as the idle SMs allow (fewer than all).  A wide CTA
+// keeps the threads per atom -- a replica moves between the classes as the
+// temperatures change, and its neighbour lists are laid out per thread of an
+// atom -- and the CTA's thread count, so that one CTA still fills an SM (a
+// smaller one could share its SM with a second and leave another SM idle);
+// its extra threads hold no atom.
+void set_wide(const re_ctx* c, LaunchCfg& k, bool on) {
+  k.wide_n = k.wide_cluster = k.wide_threads = k.wide_atom_threads = 0;
+  if (!on || c->ens.size() != 1 || c->opt.path != RE_PATH_BATCHED) return;
+  const int sms = sm_count(), wc = k.cluster * 2;
+  const int idle = sms - k.cluster * c->n_rep;
+  if (wc > 8 || idle <= 0 || (c->max_n + wc - 1) / wc < 32) return;
+  const int n = std::min(idle / k.cluster, c->n_rep - 1);
+  if (n <= 0) return;
+  k.wide_n = n;
+  k.wide_cluster = wc;
+  k.wide_atom_threads = k.atom_threads;
+  k.wide_threads = std::max(k.threads, threads_for(c->max_n, wc, k.atom_threads));
+}
+
+// The launch shape of the wide class of a split launch.
+LaunchCfg wide_cfg(const LaunchCfg& k) {
+  LaunchCfg w = k;
+  w.cluster = k.wide_cluster;
+  w.threads = k.wide_threads;
+  w.atom_threads = k.wide_atom_threads;
+  w.wide_n = w.wide_cluster = w.wide_threads = w.wide_atom_threads = 0;
+  return w;
+}
+
 // Default launch shape: enough CTAs per replica to cover the SMs in about one
 // wave, then as many threads per atom as fit in one CTA (at most 4).
 LaunchCfg default_cfg(const re_ctx* c) {
@@ -272,6 +308,7 @@ LaunchCfg default_cfg(const re_ctx* c) {
   k.threads = threads_for(c->max_n, cl, p);
   k.cell_div = 0;
   k.lists_smem = c->opt.lists_smem > 0 ? 1 : 0;
+  set_wide(c, k, c->opt.wide_launch > 0);
   return k;
 }
 
@@ -305,7 +342,8 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &s.stop, E)) ||
       (rc = dalloc(c, &s.sbuf, 7 * A)) ||
       (rc = dalloc(c, &c->d_ens, E)) || (rc = dalloc(c, &c->d_rep, R)) ||
-      (rc = dalloc(c, &c->d_work, R)) || (rc = dalloc(c, &c->d_budget, R)) ||
+      (rc = dalloc(c, &c->d_work, R)) || (rc = dalloc(c, &c->d_work2, R)) ||
+      (rc = dalloc(c, &c->d_budget, R)) ||
       (rc = dalloc(c, &c->d_budget_nx, R)) || (rc = dalloc(c, &c->d_partner, R)) ||
       (rc = dalloc(c, &c->d_acc, R)) || (rc = dalloc(c, &c->d_io, 3 * A)))
     return rc;
@@ -322,6 +360,9 @@ int allocate(re_ctx* c) {
     RE_CUDA(c, cudaMemcpy(s.fscale, ones.data(), 8 * R, cudaMemcpyHostToDevice), "init fscale");
   }
   RE_CUDA(c, cudaMallocHost(&c->h_ring, sizeof(int32_t) * R * kRing), "cudaMallocHost");
+  RE_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+  RE_CUDA(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+  RE_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
   RE_CUDA(c, cudaMallocHost(&c->h_out, (3 * 8 + 2 * 4 + 1) * R), "cudaMallocHost");
   for (int k = 0; k < kRing; ++k)
     RE_CUDA(c, cudaEventCreateWithFlags(&c->ring_ev[k], cudaEventDisableTiming), "event");
@@ -378,8 +419,16 @@ size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
 }
 
 int check_cfg(re_ctx* c, const LaunchCfg& k) {
-  if (k.cluster != 1 && k.cluster != 2 && k.cluster != 4 && k.cluster != 8)
-    return fail(c, RE_EINVAL, "cluster must be 1, 2, 4 or 8 (got %d)", k.cluster);
+  if (k.wide_n > 0) {
+    if (k.wide_n >= c->n_rep || c->ens.size() != 1 || k.wide_cluster < 2 || k.wide_cluster > 8 ||
+        k.wide_atom_threads != k.atom_threads)
+      return fail(c, RE_EINVAL, "split launch needs one ensemble, fewer wide replicas than "
+                  "replicas, 2..8 CTAs per wide replica and the same threads per atom");
+    const int rc = check_cfg(c, wide_cfg(k));
+    if (rc) return rc;
+  }
+  if (k.cluster < 1 || k.cluster > 8 || (k.cluster != 3 && (k.cluster & (k.cluster - 1))))
+    return fail(c, RE_EINVAL, "cluster must be 1, 2, 3, 4 or 8 (got %d)", k.cluster);
   if (k.atom_threads != 1 && k.atom_threads != 2 && k.atom_threads != 4 && k.atom_threads != 8)
     return fail(c, RE_EINVAL, "atom_threads must be 1, 2, 4 or 8 (got %d)", k.atom_threads);
   if (k.threads < 32 || k.threads > 1024 || k.threads % 32)
@@ -413,10 +462,31 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
     }
     // the free-running modes read the lists from global memory
     const bool budgets = async_nx <= 0 && !(fr && fr->nx > 0);
+    const bool fp64 = c->opt.precision == RE_PREC_FP64;
+    if (budgets && c->cfg.wide_n > 0) {
+      // split launch: rank by temperature on the device, then the two classes
+      // run concurrently (the wide one on the side stream, joined back)
+      const int nw = c->cfg.wide_n, nn = c->n_rep - nw;
+      const LaunchCfg wk = wide_cfg(c->cfg);
+      RE_CUDA(c, re::launch_split_work(c->s.T, c->n_rep, nw, c->d_work2, c->stream), "split work");
+      RE_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+      RE_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+      cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work2 + nn, nw, d_budget,
+                                         fp64, wk, c->max_n, c->max_ncell, list_elems_for(c, wk),
+                                         0, c->side, nullptr);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch (wide class)");
+      e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work2, nn, d_budget, fp64, c->cfg,
+                             c->max_n, c->max_ncell, list_elems_for(c, c->cfg), 0, c->stream,
+                             nullptr);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
+      RE_CUDA(c, cudaEventRecord(c->ev_join, c->side), "join");
+      RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
+      return RE_OK;
+    }
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
-                                       c->opt.precision == RE_PREC_FP64, c->cfg, c->max_n,
-                                       c->max_ncell, budgets ? list_elems_for(c, c->cfg) : 0,
-                                       async_nx, c->stream, fr);
+                                       fp64, c->cfg, c->max_n, c->max_ncell,
+                                       budgets ? list_elems_for(c, c->cfg) : 0, async_nx,
+                                       c->stream, fr);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
     return RE_OK;
   }
@@ -582,6 +652,7 @@ void re_default_opts(re_opts* o) {
   o->exch_distance = 1;
   o->id_offset = 0;
   o->lists_smem = 0;
+  o->wide_launch = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -1371,6 +1442,16 @@ int re_config_ex(const re_ctx* c, int* cluster, int* threads, int* cell_div, int
   return re_config(c, cluster, threads, cell_div, atom_threads);
 }
 
+int re_config_wide(const re_ctx* c, int* wide_n, int* wide_cluster, int* wide_threads,
+                   int* wide_atom_threads) {
+  if (!c) return RE_EINVAL;
+  if (wide_n) *wide_n = c->cfg.wide_n;
+  if (wide_cluster) *wide_cluster = c->cfg.wide_cluster;
+  if (wide_threads) *wide_threads = c->cfg.wide_threads;
+  if (wide_atom_threads) *wide_atom_threads = c->cfg.wide_atom_threads;
+  return RE_OK;
+}
+
 int re_config(const re_ctx* c, int* cluster, int* threads, int* cell_div, int* atom_threads) {
   if (!c) return RE_EINVAL;
   if (cluster) *cluster = c->cfg.cluster;
@@ -1448,8 +1529,14 @@ int re_autotune(re_ctx* c, int steps) {
         const int ls = pi & 1;
         if (c->opt.atom_threads > 0 && pvals[pi / 2] != c->opt.atom_threads) continue;
         if ((c->opt.lists_smem > 0 && ls == 0) || (c->opt.lists_smem < 0 && ls == 1)) continue;
+        for (int wv = 0; wv < 2; ++wv) {
+        // each shape as one launch, then split (hottest replicas on wider clusters)
         LaunchCfg k{clusters[ci], threads_for(c->max_n, clusters[ci], pvals[pi / 2]), m,
-                    pvals[pi / 2], ls};
+                    pvals[pi / 2], ls, 0, 0, 0, 0};
+        set_wide(c, k, wv == 1);
+        if (wv == 1 && (k.wide_n == 0 || c->opt.wide_launch < 0)) continue;
+        if (wv == 0 && c->opt.wide_launch > 0 && (set_wide(c, k, true), k.wide_n > 0)) continue;
+        if (wv == 0) set_wide(c, k, false);
         if ((c->max_n + k.cluster - 1) / k.cluster < 16) continue;
         if (check_cfg(c, k) != RE_OK) continue;
         if (ls == 1 && list_elems_for(c, k) == 0) continue;
@@ -1482,6 +1569,7 @@ int re_autotune(re_ctx* c, int steps) {
           best_ms = ms;
           best = k;
           best_m = m;
+        }
         }
       }
     }
@@ -1532,6 +1620,9 @@ void re_destroy(re_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ring) cudaFreeHost(c->h_ring);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->h_out) cudaFreeHost(c->h_out);
   for (int k = 0; k < kRing; ++k)
     if (c->ring_ev[k]) cudaEventDestroy(c->ring_ev[k]);

@@ -147,6 +147,14 @@ struct LaunchCfg {
   int cluster, threads, cell_div, atom_threads;  // CTAs per replica, threads per CTA,
                                                  // list cells per list radius, threads per atom
   int lists_smem;  // 1: each CTA's sub-lists in shared memory during a launch (when they fit)
+  // Budget mode of a one-ensemble context: the wide_n hottest replicas (by
+  // current temperature) run in a second, concurrent launch with clusters of
+  // wide_cluster CTAs (wide_threads threads each, wide_atom_threads per atom);
+  // wide_n = 0: one launch for all.  Hot replicas move faster and rebuild their lists
+  // more often (the load imbalance of the paper's Introduction): more SMs
+  // for them shorten the slowest replica, and the extra CTAs fill SMs that a
+  // uniform launch leaves idle.
+  int wide_n, wide_cluster, wide_threads, wide_atom_threads;
 };
 
 // Host helpers (re_capi.cu): list cells of an ensemble and neighbour capacities.
@@ -189,6 +197,10 @@ template <bool FP64, int P, bool LSM, int MODE>
 cudaError_t launch_batched_t(BATCHED_LAUNCH_ARGS);
 template <bool FP64, int P, bool LSM>
 int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems);
+// Work lists of a split launch: replicas ranked by decreasing temperature T
+// (ties by index); the wide_n hottest go to work[R - wide_n .. R), in rank
+// order, the others to work[0 .. R - wide_n).  One ensemble of R replicas.
+cudaError_t launch_split_work(const double* T, int R, int wide_n, int* work, cudaStream_t st);
 // applies externally decided exchange results, d_in = [T_new | lam_new |
 // vscale | uscale] (R values each, device)
 cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, cudaStream_t st);

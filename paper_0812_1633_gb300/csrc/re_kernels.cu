@@ -640,6 +640,23 @@ int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int 
   return 0;
 }
 
+__global__ void split_work_kernel(const double* __restrict__ T, int R, int wide_n, int* work) {
+  for (int a = threadIdx.x; a < R; a += blockDim.x) {
+    const double t = T[a];
+    int rank = 0;  // replicas hotter than a (ties: lower index first)
+    for (int b = 0; b < R; ++b) {
+      const double u = T[b];
+      rank += (u > t) || (u == t && b < a);
+    }
+    work[rank < wide_n ? R - wide_n + rank : rank - wide_n] = a;
+  }
+}
+
+cudaError_t launch_split_work(const double* T, int R, int wide_n, int* work, cudaStream_t st) {
+  split_work_kernel<<<1, 256, 0, st>>>(T, R, wide_n, work);
+  return cudaGetLastError();
+}
+
 __global__ void attempt_add_kernel(StateDev S, int n_ens, int n) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n_ens) S.attempt[e] += n;

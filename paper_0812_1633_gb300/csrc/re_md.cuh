@@ -371,6 +371,7 @@ __device__ int build_sublist(int i, int q, PosFn pos_hi, int N, int nc, int m, c
         const int b2 = cstart[base], e2 = cstart[base + hi2];
         const int n1 = e1 - b1, n = n1 + (e2 - b2);
         // two candidates per iteration: both loads issue before either test
+        // (four were measured slower)
         int t = q;
         for (; t + P < n; t += 2 * P) {
           const int t2 = t + P;
