@@ -106,6 +106,13 @@ typedef struct re_opts {
                        same threads per atom (re_config_wide), so the trajectories do
                        not change: the mixed path's sums are exact integers, and the
                        FP64 path differs only in the summation order of its energies. */
+  int group_launch; /* a context of several ensembles (re_group), budget mode: 0
+                       (default): one launch per ensemble, all concurrent on their own
+                       streams, each ensemble in its own launch shape (re_config_class;
+                       re_autotune tunes each on its own), so that small replicas do
+                       not run in the shape sized for the largest; -1: one launch for
+                       all replicas in one shape.  The free-running modes always use
+                       one launch (their waits stay inside it). */
 } re_opts;
 
 /* Fills *o with the defaults listed above. */
@@ -276,6 +283,13 @@ int re_config(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *a
 /* re_config and whether the neighbour lists are kept in shared memory. */
 int re_config_ex(const re_ctx *c, int *cluster, int *threads, int *cell_div, int *atom_threads,
                  int *lists_smem);
+/* Launch shape of ensemble e's launch in a context of several ensembles with
+ * per-ensemble launches (re_opts.group_launch): CTAs per replica, threads
+ * per CTA, list cells per list radius, threads per atom, lists in shared
+ * memory (any pointer may be NULL).  RE_EINVAL when e is out of range or the
+ * context runs one launch. */
+int re_config_class(const re_ctx *c, int e, int *cluster, int *threads, int *cell_div,
+                    int *atom_threads, int *lists_smem);
 /* The split launch in use (re_opts.wide_launch): replicas in the wide class,
  * CTAs per wide replica, threads per wide CTA, threads per atom in the wide
  * class (all 0: one launch).  Any pointer may be NULL. */
@@ -284,7 +298,9 @@ int re_config_wide(const re_ctx *c, int *wide_n, int *wide_cluster, int *wide_th
 /* Times candidate launch configurations (cluster, atom_threads, cell_div,
  * the lists' placement, global or shared memory, and each as one launch or
  * split, see re_opts.wide_launch) over `steps` steps each on a copy of the
- * state and keeps the fastest; the state is restored afterwards. */
+ * state and keeps the fastest; the state is restored afterwards.  With
+ * per-ensemble launches (re_opts.group_launch) every ensemble's shape is
+ * tuned on its own launch. */
 int re_autotune(re_ctx *c, int steps);
 /* Queues subsequent work on stream (a cudaStream_t; NULL: legacy default). */
 int re_set_stream(re_ctx *c, void *stream);

@@ -35,7 +35,7 @@ class _Opts(C.Structure):
                 ("pair_parity", C.c_int), ("nx", C.c_int), ("nbr_capacity", C.c_int),
                 ("cell_div", C.c_int), ("cluster", C.c_int), ("atom_threads", C.c_int),
                 ("sort_interval", C.c_int), ("exch_distance", C.c_int), ("id_offset", C.c_int),
-                ("lists_smem", C.c_int), ("wide_launch", C.c_int)]
+                ("lists_smem", C.c_int), ("wide_launch", C.c_int), ("group_launch", C.c_int)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def lib():
         L.re_lambdas.argtypes = [vp, dp]
         L.re_config_ex.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
         L.re_config_wide.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+        L.re_config_class.argtypes = [vp, C.c_int] + [C.POINTER(C.c_int)] * 5
         L.re_apply_exchange.argtypes = [vp, dp, dp, dp, dp]
         L.re_get_state.argtypes = [vp, dp, dp]
         L.re_set_state.argtypes = [vp, dp, dp]
@@ -127,7 +128,8 @@ class Context:
     def __init__(self, N, L, rc, temps, seed, *, dt=0.005, skin=0.5, tau=0.5, shift=True,
                  precision="mixed", path="batched", pair_parity=0, nx=10, nbr_capacity=0,
                  cell_div=0, cluster=0, atom_threads=0, sort_interval=0, lam=None,
-                 exch_distance=1, id_offset=0, lists_smem=0, wide_launch=0, _handle=None):
+                 exch_distance=1, id_offset=0, lists_smem=0, wide_launch=0, group_launch=0,
+                 _handle=None):
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -144,6 +146,7 @@ class Context:
             o.id_offset = id_offset
             o.lists_smem = lists_smem
             o.wide_launch = wide_launch
+            o.group_launch = group_launch
             t = np.ascontiguousarray(temps, dtype=np.float64)
             lp = None
             if lam is not None:
@@ -327,10 +330,20 @@ class Context:
                            C.byref(ls))
         wn, wc, wt, wa = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         lib().re_config_wide(self._h, C.byref(wn), C.byref(wc), C.byref(wt), C.byref(wa))
-        return {"cluster": cl.value, "threads": th.value, "cell_div": cd.value,
-                "atom_threads": at.value, "lists_smem": ls.value, "wide_n": wn.value,
-                "wide_cluster": wc.value, "wide_threads": wt.value,
-                "wide_atom_threads": wa.value}
+        cfg = {"cluster": cl.value, "threads": th.value, "cell_div": cd.value,
+               "atom_threads": at.value, "lists_smem": ls.value, "wide_n": wn.value,
+               "wide_cluster": wc.value, "wide_threads": wt.value,
+               "wide_atom_threads": wa.value}
+        classes = []
+        for e in range(self.n_ens):
+            v = [C.c_int() for _ in range(5)]
+            if lib().re_config_class(self._h, e, *[C.byref(x) for x in v]) != RE_OK:
+                break
+            classes.append(dict(zip(("cluster", "threads", "cell_div", "atom_threads",
+                                     "lists_smem"), (x.value for x in v))))
+        if classes:
+            cfg["classes"] = classes
+        return cfg
 
     def autotune(self, steps=10):
         _check(lib().re_autotune(self._h, int(steps)), self._h)

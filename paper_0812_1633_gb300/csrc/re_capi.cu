@@ -110,6 +110,14 @@ struct re_ctx {
   RepDev* d_rep = nullptr;
   int* d_work = nullptr;
   int* d_work2 = nullptr;           // split launch: work lists of the two classes
+  int* d_work_id = nullptr;         // per-ensemble launches: replica r at position r
+  int* d_work_ord = nullptr;        // budget mode, uneven budgets: longest job first
+  int32_t* d_zero = nullptr;        // n_rep zero budgets (prologue launches)
+  std::vector<LaunchCfg> ecfg;      // per-ensemble launches: the shape of each ensemble
+  int list_mode = 0;                // the lists are laid out for: 0 the uniform shape, 1 the
+                                    // per-ensemble shapes (threads per atom may differ)
+  std::vector<cudaStream_t> cls_stream;  // per-ensemble launches: ensembles 1.. run here
+  std::vector<cudaEvent_t> cls_ev;
   cudaStream_t side = nullptr;      // split launch: the wide class runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* d_budget = nullptr;      // n_rep, per call
@@ -239,6 +247,21 @@ void dfree(re_ctx* c, T*& p) {
   p = nullptr;
 }
 
+// The replicas one launch covers: every ensemble of the context (the uniform
+// launch) or one ensemble (a class of a group's per-ensemble launches).
+struct Scope {
+  int max_n, max_ncell, n_rep, e0, e1;  // ensembles [e0, e1)
+};
+
+Scope all_scope(const re_ctx* c) {
+  return Scope{c->max_n, c->max_ncell, c->n_rep, 0, (int)c->ens.size()};
+}
+
+Scope ens_scope(const re_ctx* c, int e) {
+  const EnsDev& d = c->ens[e];
+  return Scope{d.N, d.nc > 0 ? d.nc * d.nc * d.nc : 1, d.R, e, e + 1};
+}
+
 int threads_for(int max_n, int cluster, int atom_threads) {
   const int per = (max_n + cluster - 1) / cluster;
   return std::max(32, (atom_threads * per + 31) / 32 * 32);
@@ -274,6 +297,14 @@ void set_wide(const re_ctx* c, LaunchCfg& k, bool on) {
   k.wide_threads = std::max(k.threads, threads_for(c->max_n, wc, k.atom_threads));
 }
 
+// Per-ensemble launches of a group (re_opts.group_launch): in budget mode each
+// ensemble of a context of several runs as its own launch, all launches
+// concurrent on streams of their own, each in the launch shape that suits its
+// replica size.
+bool per_class(const re_ctx* c) {
+  return c->ens.size() > 1 && c->opt.group_launch >= 0 && c->opt.path == RE_PATH_BATCHED;
+}
+
 // The launch shape of the wide class of a split launch.
 LaunchCfg wide_cfg(const LaunchCfg& k) {
   LaunchCfg w = k;
@@ -286,7 +317,7 @@ LaunchCfg wide_cfg(const LaunchCfg& k) {
 
 // Default launch shape: enough CTAs per replica to cover the SMs in about one
 // wave, then as many threads per atom as fit in one CTA (at most 4).
-LaunchCfg default_cfg(const re_ctx* c) {
+LaunchCfg default_cfg(const re_ctx* c, const Scope& sc) {
   LaunchCfg k{};
   const int sms = sm_count();
   int cl = c->opt.cluster;
@@ -294,23 +325,24 @@ LaunchCfg default_cfg(const re_ctx* c) {
     // at least enough CTAs that one thread per atom fits in 1024 threads, then
     // more until the replicas cover the SMs in about one wave
     cl = 1;
-    while (cl < 8 && (c->max_n + cl - 1) / cl > 1024) cl *= 2;
-    while (cl < 8 && c->n_rep * cl < (sms * 4) / 5 && (c->max_n + 2 * cl - 1) / (2 * cl) >= 32)
+    while (cl < 8 && (sc.max_n + cl - 1) / cl > 1024) cl *= 2;
+    while (cl < 8 && sc.n_rep * cl < (sms * 4) / 5 && (sc.max_n + 2 * cl - 1) / (2 * cl) >= 32)
       cl *= 2;
   }
   int p = c->opt.atom_threads;
   if (p <= 0) {
     p = 4;
-    while (p > 1 && threads_for(c->max_n, cl, p) > 1024) p /= 2;
+    while (p > 1 && threads_for(sc.max_n, cl, p) > 1024) p /= 2;
   }
   k.cluster = cl;
   k.atom_threads = p;
-  k.threads = threads_for(c->max_n, cl, p);
+  k.threads = threads_for(sc.max_n, cl, p);
   k.cell_div = 0;
   k.lists_smem = c->opt.lists_smem > 0 ? 1 : 0;
-  set_wide(c, k, c->opt.wide_launch > 0);
+  if (sc.e1 - sc.e0 == (int)c->ens.size()) set_wide(c, k, c->opt.wide_launch > 0);
   return k;
 }
+LaunchCfg default_cfg(const re_ctx* c) { return default_cfg(c, all_scope(c)); }
 
 int upload_tables(re_ctx* c) {
   RE_CUDA(c, cudaMemcpyAsync(c->d_ens, c->ens.data(), sizeof(EnsDev) * c->ens.size(),
@@ -343,11 +375,14 @@ int allocate(re_ctx* c) {
       (rc = dalloc(c, &s.sbuf, 7 * A)) ||
       (rc = dalloc(c, &c->d_ens, E)) || (rc = dalloc(c, &c->d_rep, R)) ||
       (rc = dalloc(c, &c->d_work, R)) || (rc = dalloc(c, &c->d_work2, R)) ||
+      (rc = dalloc(c, &c->d_work_id, R)) || (rc = dalloc(c, &c->d_zero, R)) ||
+      (rc = dalloc(c, &c->d_work_ord, R)) ||
       (rc = dalloc(c, &c->d_budget, R)) ||
       (rc = dalloc(c, &c->d_budget_nx, R)) || (rc = dalloc(c, &c->d_partner, R)) ||
       (rc = dalloc(c, &c->d_acc, R)) || (rc = dalloc(c, &c->d_io, 3 * A)))
     return rc;
   RE_CUDA(c, cudaMemsetAsync(s.nbr, 0, sizeof(uint16_t) * (size_t)c->n_nbr, c->stream), "memset");
+  RE_CUDA(c, cudaMemsetAsync(c->d_zero, 0, sizeof(int32_t) * R, c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.ncnt, 0, sizeof(int32_t) * 8 * A, c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.attempt, 0, sizeof(int64_t) * E, c->stream), "memset");
   RE_CUDA(c, cudaMemsetAsync(s.pair_att, 0, sizeof(int64_t) * std::max(1, c->n_pairs), c->stream), "memset");
@@ -374,6 +409,17 @@ int allocate(re_ctx* c) {
   });
   RE_CUDA(c, cudaMemcpyAsync(c->d_work, work.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
                              c->stream), "upload work");
+  for (size_t r = 0; r < R; ++r) work[r] = (int)r;
+  RE_CUDA(c, cudaMemcpyAsync(c->d_work_id, work.data(), sizeof(int) * R, cudaMemcpyHostToDevice,
+                             c->stream), "upload work");
+  for (size_t e = 1; e < E; ++e) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    RE_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "class stream");
+    c->cls_stream.push_back(st);
+    RE_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    c->cls_ev.push_back(ev);
+  }
   std::vector<int32_t> nx(R, c->opt.nx);
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget_nx, nx.data(), sizeof(int32_t) * R,
                              cudaMemcpyHostToDevice, c->stream), "upload nx");
@@ -405,47 +451,131 @@ int max_smem_optin() {
 // Shared-memory list entries per CTA for launch shape k: the largest CTA's
 // P sub-lists over all ensembles, or 0 when they would not fit (the kernel then
 // reads the lists from global memory).
-size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
+size_t list_elems_for(const re_ctx* c, const LaunchCfg& k, const Scope& sc) {
   if (!k.lists_smem) return 0;
   const int pidx = k.atom_threads == 1 ? 0 : (k.atom_threads == 2 ? 1 : (k.atom_threads == 4 ? 2 : 3));
   size_t elems = 0;
-  for (const auto& e : c->ens) {
+  for (int i = sc.e0; i < sc.e1; ++i) {
+    const EnsDev& e = c->ens[i];
     const size_t per = (size_t)(e.N + k.cluster - 1) / k.cluster;
     elems = std::max(elems, per * k.atom_threads * (size_t)e.capsub[pidx]);
   }
-  const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
+  const size_t smem = re::batched_smem_bytes(sc.max_n, sc.max_ncell, k.threads,
                                              c->opt.precision == RE_PREC_FP64, elems);
   return smem + re::kBatchedStaticSmem <= (size_t)max_smem_optin() ? elems : 0;
 }
+size_t list_elems_for(const re_ctx* c, const LaunchCfg& k) {
+  return list_elems_for(c, k, all_scope(c));
+}
 
-int check_cfg(re_ctx* c, const LaunchCfg& k) {
+int check_cfg(re_ctx* c, const LaunchCfg& k, const Scope& sc) {
   if (k.wide_n > 0) {
     if (k.wide_n >= c->n_rep || c->ens.size() != 1 || k.wide_cluster < 2 || k.wide_cluster > 8 ||
         k.wide_atom_threads != k.atom_threads)
       return fail(c, RE_EINVAL, "split launch needs one ensemble, fewer wide replicas than "
                   "replicas, 2..8 CTAs per wide replica and the same threads per atom");
-    const int rc = check_cfg(c, wide_cfg(k));
+    const int rc = check_cfg(c, wide_cfg(k), sc);
     if (rc) return rc;
   }
   if (k.cluster < 1 || k.cluster > 8 || (k.cluster != 3 && (k.cluster & (k.cluster - 1))))
     return fail(c, RE_EINVAL, "cluster must be 1, 2, 3, 4 or 8 (got %d)", k.cluster);
   if (k.atom_threads != 1 && k.atom_threads != 2 && k.atom_threads != 4 && k.atom_threads != 8)
     return fail(c, RE_EINVAL, "atom_threads must be 1, 2, 4 or 8 (got %d)", k.atom_threads);
-  if (k.threads < 32 || k.threads > 1024 || k.threads % 32)
+  if (k.threads < 32 || k.threads > 1024 || k.threads % 32 ||
+      k.threads < k.atom_threads * ((sc.max_n + k.cluster - 1) / k.cluster))
     return fail(c, RE_EINVAL, "%d atoms per CTA x %d threads per atom exceed 1024 threads; "
-                "use more CTAs per replica", (c->max_n + k.cluster - 1) / k.cluster, k.atom_threads);
-  const size_t smem = re::batched_smem_bytes(c->max_n, c->max_ncell, k.threads,
+                "use more CTAs per replica", (sc.max_n + k.cluster - 1) / k.cluster, k.atom_threads);
+  const size_t smem = re::batched_smem_bytes(sc.max_n, sc.max_ncell, k.threads,
                                              c->opt.precision == RE_PREC_FP64, 0) +
                       re::kBatchedStaticSmem;
   const int maxsm = max_smem_optin();
   if (smem > (size_t)maxsm)
     return fail(c, RE_EINVAL, "replica of %d atoms needs %zu bytes of shared memory (max %d)",
-                c->max_n, smem, maxsm);
+                sc.max_n, smem, maxsm);
+  return RE_OK;
+}
+int check_cfg(re_ctx* c, const LaunchCfg& k) { return check_cfg(c, k, all_scope(c)); }
+
+// Launch shapes of the per-ensemble classes: each ensemble's default shape as
+// if it were a context of its own.
+void default_class_cfgs(re_ctx* c) {
+  c->ecfg.assign(c->ens.size(), LaunchCfg{});
+  for (size_t e = 0; e < c->ens.size(); ++e) {
+    c->ecfg[e] = default_cfg(c, ens_scope(c, (int)e));
+    c->ecfg[e].cell_div = c->opt.cell_div;
+  }
+}
+
+int check_class_cfgs(re_ctx* c) {
+  for (size_t e = 0; e < c->ens.size(); ++e) {
+    const int rc = check_cfg(c, c->ecfg[e], ens_scope(c, (int)e));
+    if (rc) return rc;
+  }
   return RE_OK;
 }
 
+// Cells of every ensemble from its class's cell division.
+void apply_cells_each(re_ctx* c) {
+  c->max_ncell = 1;
+  for (size_t i = 0; i < c->ens.size(); ++i) {
+    EnsDev& e = c->ens[i];
+    choose_cells(e.L, e.rlist, e.N, c->ecfg[i].cell_div, &e.nc, &e.m);
+    c->max_ncell = std::max(c->max_ncell, e.nc > 0 ? e.nc * e.nc * e.nc : 1);
+  }
+}
+
+// The launch of class e of a group's per-ensemble launches on stream st;
+// with uneven budgets its replicas longest job first.
+int launch_class(re_ctx* c, int e, const int32_t* d_budget, cudaStream_t st, bool uneven = false) {
+  const Scope sc = ens_scope(c, e);
+  const LaunchCfg& k = c->ecfg[e];
+  const int r0 = c->ens[e].rep_off;
+  const int* work = c->d_work_id + r0;
+  if (uneven && c->ens[e].R <= 4096) {
+    RE_CUDA(c, re::launch_order_work(d_budget, c->d_rep, c->d_ens, r0, c->ens[e].R,
+                                     c->d_work_ord, st), "order work");
+    work = c->d_work_ord + r0;
+  }
+  cudaError_t err = re::launch_batched(c->s, c->d_ens, c->d_rep, work, c->ens[e].R, d_budget,
+                                       c->opt.precision == RE_PREC_FP64, k, sc.max_n,
+                                       sc.max_ncell, list_elems_for(c, k, sc), 0, st, nullptr);
+  if (err != cudaSuccess) return cuda_fail(c, err, "batched MD launch (ensemble class)");
+  return RE_OK;
+}
+
+// Lists, forces, U and K of every replica in the layout of `mode` (see
+// re_ctx::list_mode) when they are in the other one: a prologue launch in the
+// new shape(s) with zero budgets.  The replicas' list rebuild counters are
+// kept (this rebuild is a change of layout, not the list rule of the
+// Example section).
+int relayout_lists(re_ctx* c, int mode) {
+  if (c->list_mode == mode) return RE_OK;
+  c->list_mode = mode;
+  const size_t R = (size_t)c->n_rep;
+  RE_CUDA(c, cudaMemcpyAsync(c->d_io, c->s.nreb, 8 * R, cudaMemcpyDeviceToDevice, c->stream),
+          "save counters");
+  RE_CUDA(c, cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream), "invalidate lists");
+  const bool fp64 = c->opt.precision == RE_PREC_FP64;
+  if (mode == 1) {
+    for (size_t e = 0; e < c->ens.size(); ++e) {
+      const int rc = launch_class(c, (int)e, c->d_zero, c->stream);
+      if (rc) return rc;
+    }
+  } else {
+    cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, c->d_zero,
+                                       fp64, c->cfg, c->max_n, c->max_ncell, 0, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
+  }
+  RE_CUDA(c, cudaMemcpyAsync(c->s.nreb, c->d_io, 8 * R, cudaMemcpyDeviceToDevice, c->stream),
+          "restore counters");
+  return RE_OK;
+}
+
+// uneven: the budgets differ between replicas (budget mode); the work is then
+// ordered longest job first on the device.
 int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
-                   int max_budget = -1, int async_nx = 0, const re::FreeDev* fr = nullptr) {
+                   int max_budget = -1, int async_nx = 0, const re::FreeDev* fr = nullptr,
+                   bool uneven = false) {
   if (c->opt.path == RE_PATH_BATCHED) {
     // renumber atoms in space order every sort_every steps (mixed path): warps
     // then hold neighbouring atoms, whose lists and gathers overlap
@@ -463,6 +593,29 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
     // the free-running modes read the lists from global memory
     const bool budgets = async_nx <= 0 && !(fr && fr->nx > 0);
     const bool fp64 = c->opt.precision == RE_PREC_FP64;
+    {
+      // a group switching between its per-ensemble launches and the uniform
+      // one (free-running modes) rebuilds its lists in the other layout first
+      const int rc = relayout_lists(c, budgets && per_class(c) ? 1 : 0);
+      if (rc) return rc;
+    }
+    if (budgets && per_class(c)) {
+      // one launch per ensemble, concurrent: class 0 on the context's stream,
+      // the others on their own streams, forked from and joined back to it
+      const int E = (int)c->ens.size();
+      RE_CUDA(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+      for (int e = 1; e < E; ++e) {
+        RE_CUDA(c, cudaStreamWaitEvent(c->cls_stream[e - 1], c->ev_fork, 0), "fork");
+        const int rc = launch_class(c, e, d_budget, c->cls_stream[e - 1], uneven);
+        if (rc) return rc;
+        RE_CUDA(c, cudaEventRecord(c->cls_ev[e - 1], c->cls_stream[e - 1]), "join");
+      }
+      const int rc = launch_class(c, 0, d_budget, c->stream, uneven);
+      if (rc) return rc;
+      for (int e = 1; e < E; ++e)
+        RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->cls_ev[e - 1], 0), "join");
+      return RE_OK;
+    }
     if (budgets && c->cfg.wide_n > 0) {
       // split launch: rank by temperature on the device, then the two classes
       // run concurrently (the wide one on the side stream, joined back)
@@ -483,8 +636,14 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
       RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
       return RE_OK;
     }
-    cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, d_budget,
-                                       fp64, c->cfg, c->max_n, c->max_ncell,
+    // uneven budgets: longest job first (otherwise the fixed order, largest
+    // replicas first)
+    const bool order = budgets && uneven && c->n_rep <= 4096;
+    if (order)
+      RE_CUDA(c, re::launch_order_work(d_budget, c->d_rep, c->d_ens, 0, c->n_rep, c->d_work_ord,
+                                       c->stream), "order work");
+    cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, order ? c->d_work_ord : c->d_work,
+                                       c->n_rep, d_budget, fp64, c->cfg, c->max_n, c->max_ncell,
                                        budgets ? list_elems_for(c, c->cfg) : 0, async_nx,
                                        c->stream, fr);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
@@ -622,8 +781,10 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
   apply_cells(c, c->opt.cell_div);
   c->cfg = default_cfg(c);
   c->cfg.cell_div = c->opt.cell_div;
+  default_class_cfgs(c);
   if (c->opt.path == RE_PATH_BATCHED) {
     int rc = check_cfg(c, c->cfg);
+    if (rc == RE_OK && per_class(c)) rc = check_class_cfgs(c);
     if (rc) return rc;
   }
   return allocate(c);
@@ -653,6 +814,7 @@ void re_default_opts(re_opts* o) {
   o->id_offset = 0;
   o->lists_smem = 0;
   o->wide_launch = 0;
+  o->group_launch = 0;
 }
 
 int re_create(int N, double L, double rc, int n_rep, const double* temps, uint64_t seed,
@@ -770,7 +932,10 @@ int re_group(re_ctx* const* ctxs, int n, re_ctx** out) {
     }
     apply_cells(c, c->opt.cell_div);
     c->cfg = default_cfg(c);
+    c->cfg.cell_div = c->opt.cell_div;
+    default_class_cfgs(c);
     if (c->opt.path == RE_PATH_BATCHED) rcode = check_cfg(c, c->cfg);
+    if (rcode == RE_OK && per_class(c)) rcode = check_class_cfgs(c);
     if (rcode == RE_OK) rcode = upload_tables(c);
   }
   // copy member states
@@ -847,9 +1012,12 @@ int re_advance(re_ctx* c, const int32_t* steps) {
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget, h, sizeof(int32_t) * c->n_rep, cudaMemcpyHostToDevice,
                              c->stream), "upload budgets");
   RE_CUDA(c, cudaEventRecord(c->ring_ev[slot], c->stream), "ring record");
-  int mx = 0;
-  for (int r = 0; r < c->n_rep; ++r) mx = std::max(mx, (int)steps[r]);
-  return launch_advance(c, c->d_budget, nullptr, mx);
+  int mx = 0, mn = INT_MAX;
+  for (int r = 0; r < c->n_rep; ++r) {
+    mx = std::max(mx, (int)steps[r]);
+    mn = std::min(mn, (int)steps[r]);
+  }
+  return launch_advance(c, c->d_budget, nullptr, mx, 0, nullptr, mn != mx);
 }
 
 int re_advance_async(re_ctx* c, int nx) {
@@ -1083,12 +1251,16 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
   }
   auto enqueue = [&]() -> int {
     for (int k = 0; k < n_cycles; ++k) {
-      int mx = c->opt.nx;
+      int mx = c->opt.nx, mn = c->opt.nx;
       if (steps) {
         mx = 0;
-        for (int r = 0; r < c->n_rep; ++r) mx = std::max(mx, (int)steps[(size_t)k * c->n_rep + r]);
+        mn = INT_MAX;
+        for (int r = 0; r < c->n_rep; ++r) {
+          mx = std::max(mx, (int)steps[(size_t)k * c->n_rep + r]);
+          mn = std::min(mn, (int)steps[(size_t)k * c->n_rep + r]);
+        }
       }
-      int rc = launch_advance(c, dbud + stride * k, nullptr, mx);
+      int rc = launch_advance(c, dbud + stride * k, nullptr, mx, 0, nullptr, mn != mx);
       if (rc) return rc;
       cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
                                           c->d_partner, c->d_acc, c->stream);
@@ -1240,16 +1412,18 @@ int re_set_state(re_ctx* c, const double* x, const double* v) {
 
 namespace {
 
-// A checkpoint: this header, then the arrays of ckpt_arrays() in order.
+// A checkpoint: this header, the launch shape of every ensemble's class (the
+// lists' layout follows the threads per atom), then the arrays of
+// ckpt_arrays() in order.
 struct CkptHeader {
   char magic[8];
   uint32_t version, precision, path, n_ens;
-  int32_t n_rep, n_pairs, plain_refresh, pad;
+  int32_t n_rep, n_pairs, plain_refresh, list_mode;
   int64_t n_atoms, n_nbr, since_sort, payload;
   LaunchCfg cfg;
   uint64_t shape;  // hash of the ensembles' parameters and the replica table
 };
-constexpr char kCkptMagic[8] = {'R', 'E', '-', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'R', 'E', '-', 'C', 'K', 'P', 'T', '2'};
 
 struct CkptArray {
   void* dev;
@@ -1291,13 +1465,13 @@ uint64_t ckpt_shape(const re_ctx* c) {
     const int64_t v[5] = {r.ens, r.id, r.atom_off, r.stream, r.nbr_off};
     mix(v, sizeof v);
   }
-  const int ov[3] = {c->opt.shift_energy, c->opt.sort_interval, c->opt.nx};
+  const int ov[4] = {c->opt.shift_energy, c->opt.sort_interval, c->opt.nx, per_class(c) ? 1 : 0};
   mix(ov, sizeof ov);
   return h;
 }
 
 size_t ckpt_bytes(re_ctx* c) {
-  size_t n = sizeof(CkptHeader);
+  size_t n = sizeof(CkptHeader) + sizeof(LaunchCfg) * c->ens.size();
   for (const CkptArray& a : ckpt_arrays(c)) n += a.bytes;
   return n;
 }
@@ -1324,6 +1498,7 @@ int re_checkpoint_save(re_ctx* c, void* buf, size_t bytes) {
   h.n_rep = c->n_rep;
   h.n_pairs = c->n_pairs;
   h.plain_refresh = c->plain_refresh ? 1 : 0;
+  h.list_mode = c->list_mode;
   h.n_atoms = c->n_atoms;
   h.n_nbr = c->n_nbr;
   h.since_sort = c->since_sort;
@@ -1333,6 +1508,8 @@ int re_checkpoint_save(re_ctx* c, void* buf, size_t bytes) {
   unsigned char* out = static_cast<unsigned char*>(buf);
   std::memcpy(out, &h, sizeof h);
   size_t off = sizeof h;
+  std::memcpy(out + off, c->ecfg.data(), sizeof(LaunchCfg) * c->ens.size());
+  off += sizeof(LaunchCfg) * c->ens.size();
   RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
   for (const CkptArray& a : ckpt_arrays(c)) {
     if (a.bytes)
@@ -1358,14 +1535,28 @@ int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
     return fail(c, RE_EINVAL, "truncated checkpoint");
   RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
   // the launch configuration first: it fixes the cells and the lists' layout
-  const int old_div = c->cfg.cell_div;
-  apply_cells(c, h.cfg.cell_div);
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  std::vector<LaunchCfg> ecfg(c->ens.size());
+  std::memcpy(ecfg.data(), in + sizeof h, sizeof(LaunchCfg) * ecfg.size());
+  const LaunchCfg old_cfg = c->cfg;
+  const std::vector<LaunchCfg> old_ecfg = c->ecfg;
+  auto cells = [&]() {
+    if (per_class(c))
+      apply_cells_each(c);
+    else
+      apply_cells(c, c->cfg.cell_div);
+  };
+  c->cfg = h.cfg;
+  c->ecfg = ecfg;
+  cells();
   int rc = check_cfg(c, h.cfg);
+  if (rc == RE_OK && per_class(c)) rc = check_class_cfgs(c);
   if (rc) {
-    apply_cells(c, old_div);
+    c->cfg = old_cfg;
+    c->ecfg = old_ecfg;
+    cells();
     return rc;
   }
-  c->cfg = h.cfg;
   c->resident_clusters = -1;
   rc = upload_tables(c);
   if (rc) return rc;
@@ -1373,8 +1564,7 @@ int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  const unsigned char* in = static_cast<const unsigned char*>(buf);
-  size_t off = sizeof h;
+  size_t off = sizeof h + sizeof(LaunchCfg) * c->ens.size();
   for (const CkptArray& a : ckpt_arrays(c)) {
     if (a.bytes)
       RE_CUDA(c, cudaMemcpy(a.dev, in + off, a.bytes, cudaMemcpyHostToDevice), "checkpoint write");
@@ -1382,6 +1572,7 @@ int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
   }
   c->since_sort = h.since_sort;
   c->plain_refresh = h.plain_refresh != 0;
+  c->list_mode = h.list_mode;
   RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
   return RE_OK;
 }
@@ -1440,6 +1631,18 @@ int re_config_ex(const re_ctx* c, int* cluster, int* threads, int* cell_div, int
   if (!c) return RE_EINVAL;
   if (lists_smem) *lists_smem = list_elems_for(c, c->cfg) > 0 ? 1 : 0;
   return re_config(c, cluster, threads, cell_div, atom_threads);
+}
+
+int re_config_class(const re_ctx* c, int e, int* cluster, int* threads, int* cell_div,
+                    int* atom_threads, int* lists_smem) {
+  if (!c || e < 0 || e >= (int)c->ens.size() || !per_class(c)) return RE_EINVAL;
+  const LaunchCfg& k = c->ecfg[e];
+  if (cluster) *cluster = k.cluster;
+  if (threads) *threads = k.threads;
+  if (cell_div) *cell_div = c->ens[e].m;
+  if (atom_threads) *atom_threads = k.atom_threads;
+  if (lists_smem) *lists_smem = list_elems_for(c, k, ens_scope(c, e)) > 0 ? 1 : 0;
+  return RE_OK;
 }
 
 int re_config_wide(const re_ctx* c, int* wide_n, int* wide_cluster, int* wide_threads,
@@ -1506,13 +1709,81 @@ int re_autotune(re_ctx* c, int steps) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   c->tuning = true;
-  const LaunchCfg keep = c->cfg;
-  const int keep_m = c->ens[0].m;
-  LaunchCfg best = keep;
-  int best_m = c->opt.cell_div;
-  float best_ms = 1e30f;
+  // One trial: restore the state, build every list of the shape (one step,
+  // untimed), then time `steps` steps with valid lists; best of two.  run(b)
+  // enqueues the launch(es) under test with budgets b.  A trial that
+  // overflowed or failed stopped early: it is never picked.
+  auto trial = [&](auto run) -> float {
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      for (auto& b : bufs)
+        cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
+      cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
+      if (run(d_one) != RE_OK) break;
+      cudaEventRecord(e0, c->stream);
+      if (run(c->d_budget) != RE_OK) break;
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t);
+    }
+    cudaGetLastError();
+    std::vector<int32_t> st(R);
+    cudaMemcpy(st.data(), c->s.status, 4 * R, cudaMemcpyDeviceToHost);
+    for (size_t r = 0; r < R; ++r)
+      if (st[r]) ms = 1e30f;
+    return ms;
+  };
   const int clusters[4] = {1, 2, 4, 8};
   const int pvals[4] = {1, 2, 4, 8};
+  const LaunchCfg keep = c->cfg;
+  LaunchCfg best = keep;
+  int best_m = c->opt.cell_div;
+  if (per_class(c)) {
+    // a group's per-ensemble launches: every class tuned on its own (the
+    // others not launched); the uniform shape, used by the free-running
+    // modes, stays the default one
+    for (size_t ei = 0; ei < c->ens.size(); ++ei) {
+      const int e = (int)ei;
+      LaunchCfg cbest = c->ecfg[e];
+      float cbest_ms = 1e30f;
+      for (int m = 0; m <= 3; ++m) {
+        if (c->opt.cell_div > 0 && m != c->opt.cell_div) continue;
+        EnsDev& d = c->ens[e];
+        int nc = 0, mm = 0;
+        choose_cells(d.L, d.rlist, d.N, m, &nc, &mm);
+        if (m > 0 && mm != m) continue;
+        c->ecfg[e].cell_div = m;
+        apply_cells_each(c);
+        upload_tables(c);
+        const Scope sc = ens_scope(c, e);
+        for (int ci = 0; ci < 4; ++ci) {
+          if (c->opt.cluster > 0 && clusters[ci] != c->opt.cluster) continue;
+          for (int pi = 0; pi < 8; ++pi) {
+            const int ls = pi & 1;
+            if (c->opt.atom_threads > 0 && pvals[pi / 2] != c->opt.atom_threads) continue;
+            if ((c->opt.lists_smem > 0 && ls == 0) || (c->opt.lists_smem < 0 && ls == 1)) continue;
+            LaunchCfg k{clusters[ci], threads_for(sc.max_n, clusters[ci], pvals[pi / 2]), m,
+                        pvals[pi / 2], ls, 0, 0, 0, 0};
+            if ((sc.max_n + k.cluster - 1) / k.cluster < 16) continue;
+            if (check_cfg(c, k, sc) != RE_OK) continue;
+            if (ls == 1 && list_elems_for(c, k, sc) == 0) continue;
+            c->ecfg[e] = k;
+            const float ms = trial([&](const int32_t* b) { return launch_class(c, e, b, c->stream); });
+            if (ms < cbest_ms) {
+              cbest_ms = ms;
+              cbest = k;
+            }
+          }
+        }
+      }
+      c->ecfg[e] = cbest;
+      apply_cells_each(c);
+      upload_tables(c);
+    }
+  } else {
+    float best_ms = 1e30f;
   for (int m = 0; m <= 3; ++m) {
     if (c->opt.cell_div > 0 && m != c->opt.cell_div) continue;
     apply_cells(c, m);
@@ -1541,30 +1812,7 @@ int re_autotune(re_ctx* c, int steps) {
         if (check_cfg(c, k) != RE_OK) continue;
         if (ls == 1 && list_elems_for(c, k) == 0) continue;
         c->cfg = k;
-        float ms = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-          // restore, force a rebuild so every trial starts alike (one step
-          // builds this shape's lists), then time a launch with valid lists
-          for (auto& b : bufs)
-            cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
-          cudaMemsetAsync(c->s.valid, 0, 4 * R, c->stream);
-          if (launch_advance(c, d_one, nullptr, 1) != RE_OK) break;
-          cudaEventRecord(e0, c->stream);
-          if (launch_advance(c, c->d_budget, nullptr) != RE_OK) break;
-          cudaEventRecord(e1, c->stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) break;
-          float t = 0;
-          cudaEventElapsedTime(&t, e0, e1);
-          ms = std::min(ms, t);
-        }
-        cudaGetLastError();
-        {
-          // a trial that overflowed or failed stopped early: never pick it
-          std::vector<int32_t> st(R);
-          cudaMemcpy(st.data(), c->s.status, 4 * R, cudaMemcpyDeviceToHost);
-          for (size_t r = 0; r < R; ++r)
-            if (st[r]) ms = 1e30f;
-        }
+        const float ms = trial([&](const int32_t* b) { return launch_advance(c, b, nullptr, 1); });
         if (ms < best_ms) {
           best_ms = ms;
           best = k;
@@ -1574,10 +1822,13 @@ int re_autotune(re_ctx* c, int steps) {
       }
     }
   }
+  }
   c->cfg = best;
   c->resident_clusters = -1;
-  apply_cells(c, best_m);
-  (void)keep_m;
+  if (per_class(c))
+    apply_cells_each(c);
+  else
+    apply_cells(c, best_m);
   upload_tables(c);
   for (auto& b : bufs) {
     cudaMemcpyAsync(b.dev, b.save, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -1621,6 +1872,8 @@ void re_destroy(re_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ring) cudaFreeHost(c->h_ring);
   if (c->side) cudaStreamDestroy(c->side);
+  for (cudaStream_t st : c->cls_stream) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : c->cls_ev) cudaEventDestroy(ev);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->h_out) cudaFreeHost(c->h_out);

@@ -201,6 +201,12 @@ int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell, size_t
 // (ties by index); the wide_n hottest go to work[R - wide_n .. R), in rank
 // order, the others to work[0 .. R - wide_n).  One ensemble of R replicas.
 cudaError_t launch_split_work(const double* T, int R, int wide_n, int* work, cudaStream_t st);
+// Work list of a budget-mode launch with uneven budgets, longest job first:
+// the replicas of [r0, r0 + n) by decreasing budget x atoms, then index,
+// written to work[r0 .. r0 + n) (n <= 4096).  A grid of many waves then ends
+// with short jobs instead of long ones started late.
+cudaError_t launch_order_work(const int32_t* budget, const RepDev* d_rep, const EnsDev* d_ens,
+                              int r0, int n, int* work, cudaStream_t st);
 // applies externally decided exchange results, d_in = [T_new | lam_new |
 // vscale | uscale] (R values each, device)
 cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, cudaStream_t st);

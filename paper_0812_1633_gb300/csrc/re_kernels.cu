@@ -15,6 +15,8 @@
 //   exchange_kernel    Implementation section: sort temperatures, pair
 //                      sorted neighbours, Metropolis with the lower-id
 //                      replica's uniform, swap T, rescale velocities.
+#include <climits>
+
 #include "re_md.cuh"
 
 namespace re {
@@ -654,6 +656,56 @@ __global__ void split_work_kernel(const double* __restrict__ T, int R, int wide_
 
 cudaError_t launch_split_work(const double* T, int R, int wide_n, int* work, cudaStream_t st) {
   split_work_kernel<<<1, 256, 0, st>>>(T, R, wide_n, work);
+  return cudaGetLastError();
+}
+
+// Longest job first: the replicas of [r0, r0 + n) ordered by decreasing
+// budget x atoms, ties by index; work[r0 + rank] = replica.  One block: the
+// (key, replica) pairs are bitonic-sorted in shared memory (n <= kOrderMax).
+constexpr int kOrderMax = 4096;
+
+__global__ void __launch_bounds__(1024) order_work_kernel(const int32_t* __restrict__ budget,
+                                                          const RepDev* __restrict__ reps,
+                                                          const EnsDev* __restrict__ ens, int r0,
+                                                          int n, int* work) {
+  __shared__ long long key[kOrderMax];
+  __shared__ int idx[kOrderMax];
+  int m = 1;
+  while (m < n) m <<= 1;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    // larger work first: sort ascending on the negated work; padding last
+    key[t] = t < n ? -(long long)budget[r0 + t] * ens[reps[r0 + t].ens].N : LLONG_MAX;
+    idx[t] = r0 + t;
+  }
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          const bool up = (t & k) == 0;  // this block of k sorts ascending
+          const long long ka = key[t], kb = key[u];
+          const int ia = idx[t], ib = idx[u];
+          const bool greater = ka > kb || (ka == kb && ia > ib);
+          if (greater == up) {
+            key[t] = kb;
+            key[u] = ka;
+            idx[t] = ib;
+            idx[u] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < n; t += blockDim.x) work[r0 + t] = idx[t];
+}
+
+cudaError_t launch_order_work(const int32_t* budget, const RepDev* d_rep, const EnsDev* d_ens,
+                              int r0, int n, int* work, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kOrderMax) return cudaErrorInvalidValue;
+  order_work_kernel<<<1, 1024, 0, st>>>(budget, d_rep, d_ens, r0, n, work);
   return cudaGetLastError();
 }
 

@@ -175,3 +175,85 @@ def test_uneven_group_full_size_sampled_match_oracle(re):
     steps, _ = g.counters()
     assert np.array_equal(steps, bud.sum(0))
     g.close()
+
+
+def test_per_ensemble_launches_equal_one_launch(re):
+    """Budget mode of a group: one launch per ensemble (each in its own shape,
+    here the same explicit shape) gives bit for bit what one launch of all
+    replicas gives (mixed path)."""
+    specs = [(256, 4, 0.7, 2.5), (500, 3, 0.7, 2.5), (864, 3, 0.7, 2.5)]
+    kw = dict(precision="mixed", skin=0.4, cluster=2, atom_threads=2, cell_div=2)
+    a = make_group(re, specs, 90, group_launch=0, **kw)
+    b = make_group(re, specs, 90, group_launch=-1, **kw)
+    assert len(a.config()["classes"]) == 3 and "classes" not in b.config()
+    Rtot = sum(s[1] for s in specs)
+    bud = inputs.random_budgets(Rtot, 4, 5, 50, 5)
+    for c in range(4):
+        for g in (a, b):
+            g.advance(bud[c])
+            g.exchange()
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.energies()[2], b.energies()[2])
+    assert np.array_equal(a.temps(), b.temps())
+
+
+def test_group_switches_between_launch_layouts(re):
+    """A group with per-ensemble launches in their default shapes (threads per
+    atom differ between the ensembles and from the uniform launch) runs budget
+    cycles, then the free-running exchange (one uniform launch), then budget
+    cycles again.  The lists are rebuilt in the other layout at each switch
+    (not counted as list-rule rebuilds); trajectories, decisions and energies
+    replay on the FP64 oracle.  Rebuild counts equal the oracle's up to the
+    first switch; after it the fresh lists' reference positions set when the
+    list rule fires next, so the counts may part."""
+    specs = [(256, 4, 0.8, 1.6), (500, 4, 0.8, 1.6)]
+    seed0, nx, A = 120, 5, 4
+    g = make_group(re, specs, seed0, precision="fp64")
+    cls = g.config()["classes"]
+    assert len(cls) == 2
+    ens = [O.Ensemble(N, inputs.box_length(N), inputs.geometric_ladder(t0, t1, R), seed0 + i)
+           for i, (N, R, t0, t1) in enumerate(specs)]
+    Rtot = sum(s[1] for s in specs)
+    r0s = np.cumsum([0] + [R for (_, R, _, _) in specs])
+
+    def budget_cycle(b):
+        g.advance(b)
+        for i, e in enumerate(ens):
+            e.advance(b[r0s[i]:r0s[i + 1]])
+
+    bud = inputs.random_budgets(Rtot, 2, 5, 30, 8)
+    budget_cycle(bud[0])
+    base, reb = g.counters()
+    assert np.array_equal(reb, np.concatenate([[r.nrebuild for r in e.reps] for e in ens]))
+    steps, T, partner, acc = g.run_free(A, nx, log=True)
+    for i, e in enumerate(ens):
+        R = specs[i][1]
+        prev = base[r0s[i]:r0s[i + 1]].copy()
+        for k in range(A):
+            st = steps[k, r0s[i]:r0s[i + 1]]
+            e.advance([int(x) for x in st - prev])
+            po, ao = e.exchange()
+            assert np.array_equal(partner[k, r0s[i]:r0s[i + 1]], po), (i, k)
+            assert np.array_equal(acc[k, r0s[i]:r0s[i + 1]].astype(bool), ao.astype(bool))
+            assert np.array_equal(T[k, r0s[i]:r0s[i + 1]], e.temps())
+            prev = st.copy()
+        # the replicas' steps after their last attempt, up to where they stopped
+        e.advance([int(x) for x in g.counters()[0][r0s[i]:r0s[i + 1]] - prev])
+    budget_cycle(bud[1])
+    x, v = g.get_state()
+    U, K, H = g.energies()
+    steps_now, rebuilds = g.counters()
+    a0 = 0
+    for i, e in enumerate(ens):
+        N, R = specs[i][0], specs[i][1]
+        L = inputs.box_length(N)
+        for k, r in enumerate(e.reps):
+            d = x[a0:a0 + N] - r.x
+            d -= L * np.rint(d / L)
+            assert np.abs(d).max() < 1e-9, (i, k)
+            assert np.abs(v[a0:a0 + N] - r.v).max() < 1e-9, (i, k)
+            assert U[r0s[i] + k] == pytest.approx(r.U, rel=1e-10)
+            assert steps_now[r0s[i] + k] == r.step
+            a0 += N
