@@ -294,22 +294,47 @@ __global__ void plain_thermo(StateDev S, const EnsDev* __restrict__ ens,
 }
 
 // ------------------------------------------------------------------ exchange
-// Sorted order of R distinct temperatures by counting (rank = number of
-// smaller values, ties broken by index).  Ts, order in shared memory.  The
-// temperatures are positive, so their IEEE bit patterns read as 64-bit
-// integers order exactly like the values: the comparisons run on the integer
-// units instead of the (1/64-rate) FP64 unit.
-__device__ void rank_sort(const double* Ts, int* order, int R) {
-  const long long* key = reinterpret_cast<const long long*>(Ts);
-  for (int a = threadIdx.x; a < R; a += blockDim.x) {
-    const long long t = key[a];
-    int rank = 0;
-    for (int b = 0; b < R; ++b) {
-      const long long u = key[b];
-      rank += (u < t) || (u == t && b < a);
-    }
-    order[rank] = a;
+// Sorted order of R distinct positive keys (ascending; ties, which the API
+// excludes, by index): a bitonic sort of (key, index) pairs over the next
+// power of two m >= R in shared memory -- keyd and order hold m entries, the
+// first R keys set by the caller, the padding sorts last.  Positive doubles
+// order like their IEEE bit patterns read as 64-bit integers, so the
+// comparisons run on the integer units instead of the (1/64-rate) FP64 unit.
+__device__ void sort_keys(double* keyd, int* order, int R) {
+  long long* key = reinterpret_cast<long long*>(keyd);
+  int m = 1;
+  while (m < R) m <<= 1;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    if (t >= R) key[t] = LLONG_MAX;
+    order[t] = t;
   }
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+          const bool up = (t & k) == 0;
+          const long long ka = key[t], kb = key[u];
+          const int ia = order[t], ib = order[u];
+          if ((ka > kb || (ka == kb && ia > ib)) == up) {
+            key[t] = kb;
+            key[u] = ka;
+            order[t] = ib;
+            order[u] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// shared memory of sort_keys for R keys
+__host__ __device__ inline size_t sort_keys_bytes(int R) {
+  size_t m = 1;
+  while (m < (size_t)R) m <<= 1;
+  return m * (sizeof(double) + sizeof(int));
 }
 
 // One exchange attempt per ensemble (one CTA each): ladder keys T/lam sorted,
@@ -322,15 +347,17 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
   extern __shared__ __align__(16) unsigned char sh[];
   const EnsDev E = ens[blockIdx.x];
   const int R = E.R, base = E.rep_off;
+  int m = 1;
+  while (m < R) m <<= 1;
   double* key = reinterpret_cast<double*>(sh);
-  int* order = reinterpret_cast<int*>(key + R);
+  int* order = reinterpret_cast<int*>(key + m);
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
     key[a] = S.T[base + a] / S.lam[base + a];
     if (partner_out) partner_out[base + a] = -1;
     if (acc_out) acc_out[base + a] = 0;
   }
   __syncthreads();
-  rank_sort(key, order, R);
+  sort_keys(key, order, R);
   __syncthreads();
   const int64_t attempt = S.attempt[blockIdx.x];
   const int p = pair_offset(E.parity_mode, E.seed, attempt);
@@ -387,8 +414,10 @@ __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
                                     int32_t* partner, uint8_t* acc, double* vscale,
                                     double* uscale) {
   extern __shared__ __align__(16) unsigned char sh[];
+  int m = 1;
+  while (m < R) m <<= 1;
   double* key = reinterpret_cast<double*>(sh);
-  int* order = reinterpret_cast<int*>(key + R);
+  int* order = reinterpret_cast<int*>(key + m);
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
     const double l = lam ? lam[a] : 1.0;
     key[a] = T[a] / l;
@@ -400,7 +429,7 @@ __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
     if (uscale) uscale[a] = 1.0;
   }
   __syncthreads();
-  rank_sort(key, order, R);
+  sort_keys(key, order, R);
   __syncthreads();
   const int p = pair_offset(mode, seed, attempt);
   const int d = max(1, distance);
@@ -795,7 +824,12 @@ cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, 
 
 cudaError_t launch_exchange(const StateDev& s, const EnsDev* d_ens, int n_ens, int max_r,
                             int32_t* d_partner, uint8_t* d_acc, cudaStream_t st) {
-  const size_t smem = (size_t)max_r * (sizeof(double) + sizeof(int));
+  const size_t smem = sort_keys_bytes(max_r);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(exchange_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const int threads = max_r >= 512 ? 512 : ((max_r + 31) / 32) * 32;
   exchange_kernel<<<n_ens, threads, smem, st>>>(s, d_ens, d_partner, d_acc);
   return cudaGetLastError();
@@ -854,7 +888,7 @@ cudaError_t launch_exchange_raw(int R, const double* T, const double* lam, const
                                 double* T_out, double* lam_out, int32_t* partner,
                                 uint8_t* accepted, double* vscale, double* uscale,
                                 cudaStream_t st) {
-  const size_t smem = (size_t)R * (sizeof(double) + sizeof(int));
+  const size_t smem = sort_keys_bytes(R);
   const int threads = R >= 512 ? 512 : ((R + 31) / 32) * 32;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(exchange_raw_kernel,
