@@ -576,6 +576,94 @@ def run_drift(args):
     print(json.dumps(out), flush=True)
 
 
+# The precision study of the 256 x 4000 workload (T 0.75-1.8): its 16 coldest
+# replicas (consecutive on the 256-replica ladder), N = 4000, FCC start.
+PREC_N, PREC_R, PREC_SEED = 4000, 16, 12345
+
+
+def precision_temps():
+    return inputs.geometric_ladder(0.75, 1.8, 256)[:PREC_R]
+
+
+def drift_run(ctx, steps, chunk, N, dt=0.005, budgets=None):
+    """H~/N sampled every `chunk` steps; returns the least-squares slope per
+    replica (per atom per tau) and the wall time."""
+    t, H = [], []
+    t0 = time.perf_counter()
+    for c in range(steps // chunk):
+        ctx.advance(chunk if budgets is None else budgets * chunk)
+        H.append(ctx.energies()[2])
+        t.append((c + 1) * chunk * dt)
+    return drift_slopes(t, H, N), time.perf_counter() - t0
+
+
+def exchange_run(ctx, cycles, nx, N, dt=0.005, sample=10):
+    """cycles x (advance nx, exchange): acceptance per ladder pair and H~ slope
+    (H~ stays continuous across exchanges)."""
+    att0, acc0 = ctx.accept_stats()
+    t, H = [], []
+    t0 = time.perf_counter()
+    for c in range(cycles):
+        ctx.advance(nx)
+        ctx.exchange()
+        if (c + 1) % sample == 0:
+            H.append(ctx.energies()[2])
+            t.append((c + 1) * nx * dt)
+    att, acc = ctx.accept_stats()
+    return ((acc - acc0) / np.maximum(att - att0, 1)).tolist(), (att - att0).tolist(), \
+        drift_slopes(t, H, N), time.perf_counter() - t0
+
+
+def run_precision(args):
+    """Precision study (the 256 x 4000 workload's precision configuration):
+    energy drift of H~ per atom per tau over equal-length runs for the mixed
+    batched, FP64 batched and plain FP64 paths, and exchange acceptance per
+    ladder pair for the two batched paths.  The oracle's legs run on the host
+    (tests/precision_oracle.py, the oracle being test infrastructure)."""
+    import torch
+    import paper_0812_1633_gb300 as re
+    from paper_0812_1633_gb300 import build
+    build.build()
+    N, R, S = PREC_N, PREC_R, args.prec_steps
+    L = inputs.box_length(N)
+    temps = precision_temps()
+    out = {"study": "precision: energy drift and exchange acceptance per path",
+           "workload": f"{R} consecutive replicas (the coldest) of the 256-replica ladder T "
+                       f"0.75-1.8, N {N}, rho 0.8442, dt 0.005, tau_T 0.5, skin 0.5, FCC start, "
+                       f"seed {PREC_SEED}",
+           "drift": {"steps": S, "unit": "H~ slope per atom per tau (least squares)"},
+           "exchange": {"steps": S, "nx": 10}}
+    ends = np.zeros(R, np.int32)
+    ends[[0, R - 1]] = 1
+    for name, kw in [("mixed_batched", dict(precision="mixed")),
+                     ("fp64_batched", dict(precision="fp64")),
+                     ("plain_fp64", dict(path="plain"))]:
+        ctx = re.Context(N, L, 2.5, temps, PREC_SEED, **kw)
+        if name == "plain_fp64":
+            # one replica per launch sequence: the two ends of the ladder only
+            sl, wall = drift_run(ctx, S, 100, N, budgets=ends)
+            sl = sl[[0, R - 1]]
+            reps = [0, R - 1]
+        else:
+            sl, wall = drift_run(ctx, S, 100, N)
+            reps = list(range(R))
+        out["drift"][name] = {"replicas": reps, "slopes": sl.tolist(),
+                              "mean": float(np.mean(sl)), "max_abs": float(np.abs(sl).max()),
+                              "replica_atom_steps_per_s": len(reps) * N * S / wall}
+        ctx.close()
+        print(json.dumps({name: out["drift"][name]}), flush=True)
+    for name, kw in [("mixed_batched", dict(precision="mixed")),
+                     ("fp64_batched", dict(precision="fp64"))]:
+        ctx = re.Context(N, L, 2.5, temps, PREC_SEED, **kw)
+        acc, att, sl, wall = exchange_run(ctx, S // 10, 10, N)
+        out["exchange"][name] = {"acceptance_per_pair": acc, "attempts_per_pair": att,
+                                 "slopes": sl.tolist(), "mean_slope": float(np.mean(sl)),
+                                 "wall_s": wall}
+        ctx.close()
+        print(json.dumps({name + "_exchange": out["exchange"][name]}), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def melted_context(re, N, temps, seed, **kw):
     """A liquid on the ladder: melted at T 2.0-2.2 from the FCC start, velocities
     rescaled to the ladder, 200 steps on it."""
@@ -803,13 +891,13 @@ def run_diffusion(args):
 # capture per workload and launch shape (profiles/md_batched_kernel_64x864.md),
 # valid only while the kernel's sources are the ones that were profiled.
 PROFILED_TRAFFIC = {
-    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "bd1533beafd5c35e",
-                                 "bytes_per_launch": 14035968 + 5120,
+    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "ee42eef8846e6693",
+                                 "bytes_per_launch": 14040064 + 3328,
                                  # pipe use over the SMs' active cycles (ncu --set full)
-                                 "pipes": {"fma_pct": 25.77, "alu_pct": 38.32, "fp64_pct": 5.51,
-                                           "issue_active_pct": 60.64,
-                                           "smem_wavefronts": 20908454,
-                                           "smem_bank_conflicts": 8653888}},
+                                 "pipes": {"fma_pct": 25.41, "alu_pct": 41.85, "fp64_pct": 5.12,
+                                           "issue_active_pct": 61.89,
+                                           "smem_wavefronts": 21273541,
+                                           "smem_bank_conflicts": 8760613}},
 }
 
 
@@ -818,7 +906,8 @@ def kernel_sources_hash():
     h = hashlib.sha256()
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_0812_1633_gb300",
                         "csrc")
-    for f in ("re_kernels.cu", "re_device.cuh", "re_internal.h"):
+    for f in ("re_md.cuh", "re_batched.cuh", "re_batched_mix.cu", "re_device.cuh",
+              "re_internal.h"):
         with open(os.path.join(here, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -855,7 +944,8 @@ def main():
                     help="cycles of the CUDA-graph replay measurement (0: skip)")
     ap.add_argument("--free-attempts", type=int, default=200,
                     help="exchange attempts of the free-running measurement (0: skip)")
-    ap.add_argument("--study", default=None, choices=["drift", "lambda", "diffusion", "acceptance"],
+    ap.add_argument("--study", default=None,
+                    choices=["drift", "lambda", "diffusion", "acceptance", "precision"],
                     help="run a study instead of the throughput bench")
     ap.add_argument("--lam-n", type=int, default=864)
     ap.add_argument("--lam-nx", type=int, default=5)
@@ -870,6 +960,7 @@ def main():
     ap.add_argument("--acc-r", type=int, default=8)
     ap.add_argument("--acc-samples", type=int, default=4000)
     ap.add_argument("--acc-attempts", type=int, default=2000)
+    ap.add_argument("--prec-steps", type=int, default=100000)
     ap.add_argument("--drift-n", type=int, default=4000)
     ap.add_argument("--drift-r", type=int, default=8)
     ap.add_argument("--drift-steps", type=int, default=20000)
@@ -893,6 +984,9 @@ def main():
         return
     if args.study == "acceptance":
         run_acceptance(args)
+        return
+    if args.study == "precision":
+        run_precision(args)
         return
     if args.impl == "reference":
         run_reference(args, cfg)
