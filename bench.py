@@ -273,6 +273,18 @@ def in_cutoff_pairs_per_atom(x, cfg, n_sample=8, rc=2.5):
     return tot_pairs / tot_atoms
 
 
+def equilibrate(ctx, steps, chunk=100):
+    """Untimed MD from the FCC start, no exchanges: the timed cycles then see
+    the liquid's list-rebuild rate rather than that of the lattice's first
+    steps (at N_x = 1 on the 1024 x 2048 workload the first hundred steps run
+    about 15 % faster than the liquid)."""
+    done = 0
+    while done < steps:
+        n = min(chunk, steps - done)
+        ctx.advance(n)
+        done += n
+
+
 def run_gpu(args, cfg):
     import torch
     import paper_0812_1633_gb300 as re
@@ -305,6 +317,7 @@ def run_gpu(args, cfg):
             for m in members:
                 m.close()
         c.set_stream(stream)
+        equilibrate(c, args.equil_steps)
         return c
 
     skin_trials = None
@@ -322,15 +335,13 @@ def run_gpu(args, cfg):
                 return float(t.item())
         skin, ctx, skin_trials = tune.choose_skin(make, cycles=20, budgets=tb, agree=agree)
         tuned = ctx.config()
-    else:
+    elif args.launch:
         skin = 0.5 if skin == "auto" else skin
-        ctx = make(skin)
-    if args.launch:
         cl, at, cd = (int(v) for v in args.launch.split(","))
-        ctx.close()
         ctx = make(skin, cluster=cl, atom_threads=at, cell_div=cd, wide_launch=args.wide)
         tuned = ctx.config()
-    elif skin_trials is None:
+    else:
+        ctx = make(skin)
         tuned = ctx.autotune(steps=40)
     Rtot = ctx.n_rep
     W, K = args.warmup, args.steps
@@ -380,18 +391,24 @@ def run_gpu(args, cfg):
     achieved = flops_per_launch / adv_mean_s / 1e12
     peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
 
-    # ---- e2e: public API with host buffers every step
+    # ---- e2e: the public API with host buffers every cycle.  re_run_record
+    # copies each cycle's budgets host -> device (pinned) and each cycle's
+    # record (partners, accepted flags, T, U, K, econs) device -> host on copy
+    # streams beside the compute stream; the call returns once the last record
+    # is on the host.  One untimed call first sizes its buffers.
+    nE = max(3, min(K, 100))
+    bE = np.stack([budgets[W + (k % K)] for k in range(nE)])
+    ctx.run_record(nE, bE)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t_e2e0 = time.perf_counter()
-    nE = max(3, min(K, 20))
-    for k in range(nE):
-        ctx.advance(budgets[W + (k % K)])
-        ctx.exchange(outputs=True)
-        ctx.energies()
+    ctx.run_record(nE, bE)
     t_e2e = time.perf_counter() - t_e2e0
-    e2e_work = sum(atoms_per_cycle(cfg, budgets[W + (k % K)]) for k in range(nE))
+    e2e_work = sum(atoms_per_cycle(cfg, bE[k]) for k in range(nE))
     _, e2e_value = aggregate(t_e2e, e2e_work, ws, dist)  # slowest rank's time, all ranks' work
     h2d = 4 * Rtot
-    d2h = 4 * Rtot + Rtot + 3 * 8 * Rtot + 4 * Rtot
+    d2h = (37 * Rtot + 7) // 8 * 8   # one record row: 4 doubles, an int32 and a byte per replica
 
     # ---- the same cycles replayed as one captured CUDA graph (re_run with a
     # graph): the host enqueues one graph instead of two launches per cycle
@@ -494,6 +511,8 @@ def run_gpu(args, cfg):
             "data": "synthetic (FCC start at rho 0.8442, seeded Philox velocities and budgets)",
             "config": {"workload": desc, "path": f"{prec} batched (one persistent launch per cycle)",
                        "l2": "flushed between timed steps (256 MB write)",
+                       "equilibration": f"{args.equil_steps} untimed MD steps from the FCC start "
+                                        f"before tuning and timing",
                        "launch": tuned, "parallelism": f"replicas, {ws} independent ensemble(s)",
                        "skin": skin, "skin_trials_ms_per_cycle": skin_trials},
             "exch_per_s": exch_per_s,
@@ -511,7 +530,8 @@ def run_gpu(args, cfg):
             "plain_fp64": plain,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "replica·atom-steps/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "cycles": nE,
+                    "call": "re_run_record (budgets in, per-cycle record out)"},
             "async": free,
             "graph": graph,
             # per step: the advance (one launch, or the ranking kernel and the
@@ -891,7 +911,7 @@ def run_diffusion(args):
 # capture per workload and launch shape (profiles/md_batched_kernel_64x864.md),
 # valid only while the kernel's sources are the ones that were profiled.
 PROFILED_TRAFFIC = {
-    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "ee42eef8846e6693",
+    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "8b34f234f83f911c",
                                  "bytes_per_launch": 14040064 + 3328,
                                  # pipe use over the SMs' active cycles (ncu --set full)
                                  "pipes": {"fma_pct": 25.41, "alu_pct": 41.85, "fp64_pct": 5.12,
@@ -935,6 +955,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--equil-steps", type=int, default=1000,
+                    help="untimed MD steps from the FCC start before tuning and timing")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c1", choices=sorted(CONFIGS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -228,6 +228,21 @@ int re_exchange(re_ctx *c, int32_t *partner_out, uint8_t *accepted_out);
  * the launches of all cycles in one CUDA graph and replays it. */
 int re_run(re_ctx *c, int n_cycles, const int32_t *steps, int use_graph);
 
+/* re_run with the run's log read back every cycle (the Example section's
+ * record of a replica-exchange run: who exchanged, and the energies and
+ * temperatures after every attempt).  Cycle k: row k of the budgets is
+ * copied host -> device (steps: host, n_cycles x n_rep; NULL: opt.nx), the
+ * replicas advance, one exchange attempt runs, and the cycle's record is
+ * copied device -> host.  The copies run on two streams of their own and
+ * overlap the following cycles; the call returns when the last record has
+ * arrived (synchronous).  Outputs (host, n_cycles x n_rep each, row k =
+ * cycle k, replica ids as in re_exchange; any may be NULL): partner id (-1:
+ * unpaired), accepted flag, temperature after the attempt, U, K and H~ (as
+ * re_energies would report after the attempt).  Errors as re_run; a replica
+ * error (status) is reported after the last cycle, the outputs written. */
+int re_run_record(re_ctx *c, int n_cycles, const int32_t *steps, int32_t *partner,
+                  uint8_t *accepted, double *T, double *U, double *K, double *H);
+
 /* Per replica (host, n_rep each, K and H may be NULL): potential energy U,
  * kinetic energy K and H~ = U + K + (energy removed by the thermostat). */
 int re_energies(re_ctx *c, double *U, double *K, double *H);

@@ -152,6 +152,16 @@ struct re_ctx {
   double wait_s = 1.0;         // limit of the free-running exchange's bounded waits
   int stall_rep = -1;          // fault injection for the next re_run_free (-1: none)
   int stall_from = 0;
+  // re_run_record: the record rows (device, pinned host), the staged budgets,
+  // and two copy streams (host -> device budgets, device -> host records)
+  unsigned char* d_rec = nullptr;
+  unsigned char* h_rec = nullptr;
+  size_t rec_cap = 0;               // bytes of d_rec and h_rec
+  int32_t* d_rec_bud = nullptr;
+  int32_t* h_rec_bud = nullptr;
+  size_t rec_bud_cap = 0;           // entries of d_rec_bud and h_rec_bud
+  cudaStream_t rec_in = nullptr, rec_out = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // cached graph of re_run
   cudaGraphExec_t graph = nullptr;
   int graph_cycles = 0;
@@ -1304,6 +1314,121 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
   return RE_OK;
 }
 
+namespace {
+
+// Frees a device buffer of the context's allocation list.
+void dfree_tracked(re_ctx* c, void* p) {
+  if (!p) return;
+  cudaFree(p);
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+}
+
+}  // namespace
+
+int re_run_record(re_ctx* c, int n_cycles, const int32_t* steps, int32_t* partner,
+                  uint8_t* accepted, double* T, double* U, double* K, double* H) {
+  ApiRange range_("re_run_record");
+  if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
+  if (n_cycles < 0) return fail(c, RE_EINVAL, "n_cycles must be >= 0");
+  if (n_cycles == 0) return RE_OK;
+  const size_t R = (size_t)c->n_rep, nb = (size_t)n_cycles * R;
+  if (steps)
+    for (size_t i = 0; i < nb; ++i)
+      if (steps[i] < 0) return fail(c, RE_EINVAL, "negative step budget");
+  const bool plain = c->opt.path == RE_PATH_PLAIN;
+  // record row: T, U, K, econs (doubles), partner (int32), accepted (bytes)
+  const size_t rowb = (37 * R + 7) & ~(size_t)7;
+  const size_t off_part = 32 * R, off_acc = 36 * R;
+  if (rowb * n_cycles > c->rec_cap || (steps && !plain && nb > c->rec_bud_cap)) {
+    RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+    if (rowb * n_cycles > c->rec_cap) {
+      dfree_tracked(c, c->d_rec);
+      c->d_rec = nullptr;
+      if (c->h_rec) cudaFreeHost(c->h_rec);
+      c->h_rec = nullptr;
+      c->rec_cap = 0;
+      int rc = dalloc(c, &c->d_rec, rowb * n_cycles);
+      if (rc) return rc;
+      RE_CUDA(c, cudaMallocHost(&c->h_rec, rowb * n_cycles), "cudaMallocHost");
+      c->rec_cap = rowb * n_cycles;
+    }
+    if (steps && !plain && nb > c->rec_bud_cap) {
+      dfree_tracked(c, c->d_rec_bud);
+      c->d_rec_bud = nullptr;
+      if (c->h_rec_bud) cudaFreeHost(c->h_rec_bud);
+      c->h_rec_bud = nullptr;
+      c->rec_bud_cap = 0;
+      int rc = dalloc(c, &c->d_rec_bud, nb);
+      if (rc) return rc;
+      RE_CUDA(c, cudaMallocHost(&c->h_rec_bud, sizeof(int32_t) * nb), "cudaMallocHost");
+      c->rec_bud_cap = nb;
+    }
+  }
+  if (!c->rec_in) {
+    RE_CUDA(c, cudaStreamCreateWithFlags(&c->rec_in, cudaStreamNonBlocking), "stream");
+    RE_CUDA(c, cudaStreamCreateWithFlags(&c->rec_out, cudaStreamNonBlocking), "stream");
+    RE_CUDA(c, cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "event");
+    RE_CUDA(c, cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "event");
+  }
+  // a previous call that failed half-way may still be copying
+  RE_CUDA(c, cudaStreamSynchronize(c->rec_in), "synchronise");
+  RE_CUDA(c, cudaStreamSynchronize(c->rec_out), "synchronise");
+  if (steps && !plain) std::memcpy(c->h_rec_bud, steps, sizeof(int32_t) * nb);
+  for (int k = 0; k < n_cycles; ++k) {
+    const int32_t* hrow = steps ? steps + (size_t)k * R : nullptr;
+    int rc;
+    if (plain) {
+      rc = launch_advance(c, nullptr, hrow);
+    } else if (hrow) {
+      int mx = 0, mn = INT_MAX;
+      for (size_t r = 0; r < R; ++r) {
+        mx = std::max(mx, (int)hrow[r]);
+        mn = std::min(mn, (int)hrow[r]);
+      }
+      // this cycle's budgets: their own copy, which the advance waits for
+      int32_t* drow = c->d_rec_bud + (size_t)k * R;
+      RE_CUDA(c, cudaMemcpyAsync(drow, c->h_rec_bud + (size_t)k * R, sizeof(int32_t) * R,
+                                 cudaMemcpyHostToDevice, c->rec_in), "upload budgets");
+      RE_CUDA(c, cudaEventRecord(c->ev_in, c->rec_in), "event");
+      RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_in, 0), "event wait");
+      rc = launch_advance(c, drow, nullptr, mx, 0, nullptr, mn != mx);
+    } else {
+      rc = launch_advance(c, c->d_budget_nx, nullptr, c->opt.nx);
+    }
+    if (rc) return rc;
+    unsigned char* row = c->d_rec + (size_t)k * rowb;
+    cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
+                                        reinterpret_cast<int32_t*>(row + off_part), row + off_acc,
+                                        c->stream, reinterpret_cast<double*>(row), (int)R);
+    if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+    // the record of cycle k travels while cycle k + 1 runs
+    RE_CUDA(c, cudaEventRecord(c->ev_out, c->stream), "event");
+    RE_CUDA(c, cudaStreamWaitEvent(c->rec_out, c->ev_out, 0), "event wait");
+    RE_CUDA(c, cudaMemcpyAsync(c->h_rec + (size_t)k * rowb, row, rowb, cudaMemcpyDeviceToHost,
+                               c->rec_out), "read record");
+  }
+  RE_CUDA(c, cudaEventRecord(c->ev_out, c->rec_out), "event");
+  RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
+  const int rc = status_check(c);  // synchronises the stream, and so the copies
+  if (rc != RE_OK && rc != RE_ENUMERIC && rc != RE_EOVERFLOW) return rc;
+  for (int k = 0; k < n_cycles; ++k) {
+    const unsigned char* row = c->h_rec + (size_t)k * rowb;
+    const double* d = reinterpret_cast<const double*>(row);
+    const int32_t* pr = reinterpret_cast<const int32_t*>(row + off_part);
+    const size_t o = (size_t)k * R;
+    for (size_t r = 0; r < R; ++r) {
+      if (T) T[o + r] = d[r];
+      if (U) U[o + r] = d[R + r];
+      if (K) K[o + r] = d[2 * R + r];
+      if (H) H[o + r] = d[R + r] + d[2 * R + r] + d[3 * R + r];
+      if (partner) partner[o + r] = pr[r];
+      if (accepted) accepted[o + r] = row[off_acc + r];
+    }
+  }
+  return rc;
+}
+
 int re_energies(re_ctx* c, double* U, double* K, double* H) {
   ApiRange range_("re_energies");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
@@ -1871,6 +1996,8 @@ const char* re_last_error(const re_ctx* c) {
 void re_destroy(re_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->rec_in) cudaStreamSynchronize(c->rec_in);
+  if (c->rec_out) cudaStreamSynchronize(c->rec_out);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_ring) cudaFreeHost(c->h_ring);
@@ -1880,6 +2007,12 @@ void re_destroy(re_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->h_out) cudaFreeHost(c->h_out);
+  if (c->h_rec) cudaFreeHost(c->h_rec);
+  if (c->h_rec_bud) cudaFreeHost(c->h_rec_bud);
+  if (c->rec_in) cudaStreamDestroy(c->rec_in);
+  if (c->rec_out) cudaStreamDestroy(c->rec_out);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (int k = 0; k < kRing; ++k)
     if (c->ring_ev[k]) cudaEventDestroy(c->ring_ev[k]);
   delete c;

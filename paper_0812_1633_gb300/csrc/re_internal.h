@@ -215,8 +215,10 @@ cudaError_t launch_attempt_add(const StateDev& s, int n_ens, int n, cudaStream_t
 cudaError_t launch_plain_advance(const StateDev& s, const EnsDev& e, const RepDev& r, int rep,
                                  const EnsDev* d_ens, const RepDev* d_rep, int steps,
                                  int max_ncell, cudaStream_t st, int refresh);
+// d_rec (may be null): record row of rtot replicas, see exchange_kernel
 cudaError_t launch_exchange(const StateDev& s, const EnsDev* d_ens, int n_ens, int max_r,
-                            int32_t* d_partner, uint8_t* d_acc, cudaStream_t st);
+                            int32_t* d_partner, uint8_t* d_acc, cudaStream_t st,
+                            double* d_rec = nullptr, int rtot = 0);
 cudaError_t launch_apply_vscale(const StateDev& s, const RepDev* d_rep, const EnsDev* d_ens,
                                 int n_rep, cudaStream_t st);
 cudaError_t launch_export_state(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,

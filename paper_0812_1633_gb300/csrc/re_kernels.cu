@@ -337,53 +337,105 @@ __host__ __device__ inline size_t sort_keys_bytes(int R) {
   return m * (sizeof(double) + sizeof(int));
 }
 
+// Ladders up to this size are ordered by counting ranks (every thread scans
+// all keys, broadcast reads, no barriers); longer ones by sort_keys.
+constexpr int kRankSortMax = 256;
+
+// shared memory of exchange_kernel for R replicas: sort_keys' area, then per
+// replica the quotients lam/T and U/lam, the exchange uniform, T and lam
+__host__ __device__ inline size_t exchange_smem_bytes(int R) {
+  return sort_keys_bytes(R) + (size_t)R * 5 * sizeof(double);
+}
+
 // One exchange attempt per ensemble (one CTA each): ladder keys T/lam sorted,
 // pairs (q, q + d) of the ladder (d = 1: sorted neighbours), the Metropolis
 // rule, and on acceptance the parameter sets (T, lam) are swapped: the
 // velocities take the pending factor sqrt(T_new/T_old), the forces
 // lam_new/lam_old, K and U follow and econs absorbs both changes.
+// The kernel is a short chain of dependent steps on one CTA, so it is laid
+// out for latency: one load phase, every per-replica quotient and uniform
+// computed once and in parallel (the same operations as the pair formula, so
+// the decisions are those of metropolis()), and what an accepted pair
+// changes read before the decision.
+// rec (may be null): the cycle's record row, per replica id of all rtot
+// replicas T, U, K and econs after the attempt at rec[0..4 rtot).
 __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int32_t* partner_out,
-                                uint8_t* acc_out) {
+                                uint8_t* acc_out, double* rec, int rtot) {
   extern __shared__ __align__(16) unsigned char sh[];
-  const EnsDev E = ens[blockIdx.x];
-  const int R = E.R, base = E.rep_off;
+  const int R = ens[blockIdx.x].R, base = ens[blockIdx.x].rep_off;
+  const int pair_off = ens[blockIdx.x].pair_off, xdist = ens[blockIdx.x].xdist;
+  const int parity_mode = ens[blockIdx.x].parity_mode;
+  const uint64_t seed = ens[blockIdx.x].seed;
+  const int64_t attempt = S.attempt[blockIdx.x];
   int m = 1;
   while (m < R) m <<= 1;
   double* key = reinterpret_cast<double*>(sh);
   int* order = reinterpret_cast<int*>(key + m);
+  double* qt = reinterpret_cast<double*>(sh + sort_keys_bytes(R));  // lam / T
+  double* qu = qt + R;                                               // U / lam
+  double* uni = qu + R;                                              // uniform of id a
+  double* Tsh = uni + R;
+  double* lsh = Tsh + R;
   for (int a = threadIdx.x; a < R; a += blockDim.x) {
-    key[a] = S.T[base + a] / S.lam[base + a];
+    const double T = S.T[base + a], lam = S.lam[base + a], U = S.U[base + a];
+    const bool one = lam == 1.0;  // x / 1 == x exactly: the divisions are skipped
+    key[a] = one ? T : T / lam;
+    qt[a] = __ddiv_rn(lam, T);
+    qu[a] = one ? U : __ddiv_rn(U, lam);
+    uni[a] = uniforms(seed, (uint64_t)a, (uint64_t)attempt, kTagExch, 0ull).u0;
+    Tsh[a] = T;
+    lsh[a] = lam;
     if (partner_out) partner_out[base + a] = -1;
     if (acc_out) acc_out[base + a] = 0;
   }
   __syncthreads();
-  sort_keys(key, order, R);
+  if (R <= kRankSortMax) {
+    // positive doubles order like their bit patterns; ties (excluded by the
+    // API) by index, as sort_keys
+    const long long* ki = reinterpret_cast<const long long*>(key);
+    for (int a = threadIdx.x; a < R; a += blockDim.x) {
+      const long long ka = ki[a];
+      int rank = 0;
+#pragma unroll 8
+      for (int b = 0; b < R; ++b) {
+        const long long kb = ki[b];
+        rank += (kb < ka) | ((kb == ka) & (b < a));
+      }
+      order[rank] = a;
+    }
+  } else {
+    sort_keys(key, order, R);
+  }
   __syncthreads();
-  const int64_t attempt = S.attempt[blockIdx.x];
-  const int p = pair_offset(E.parity_mode, E.seed, attempt);
-  const int d = max(1, E.xdist);
+  const int p = pair_offset(parity_mode, seed, attempt);
+  const int d = max(1, xdist);
   for (int q = threadIdx.x; q < R; q += blockDim.x) {
     const int qb = ladder_partner(q, R, p, d);
     if (qb <= q) continue;  // unpaired, or the upper member of its pair
     const int a = order[q], b = order[qb];
     const int ga = base + a, gb = base + b;
-    const double Ta = S.T[ga], Tb = S.T[gb], la = S.lam[ga], lb = S.lam[gb];
-    const bool ok = metropolis(Ta, Tb, la, lb, S.U[ga], S.U[gb], E.seed, min(a, b), attempt);
+    // everything an accepted exchange changes, requested before the decision
+    const long long n_att = S.pair_att[pair_off + q], n_acc = S.pair_acc[pair_off + q];
+    const double Ka = S.K[ga], Kb = S.K[gb], Ea = S.econs[ga], Eb = S.econs[gb];
+    const double va = S.vscale[ga], vb = S.vscale[gb];
+    const double Ta = Tsh[a], Tb = Tsh[b], la = lsh[a], lb = lsh[b];
+    // metropolis(): D = (lam_a/T_a - lam_b/T_b)(U_a/lam_a - U_b/lam_b), accept
+    // iff D >= 0 or r < exp(D), r the uniform of the lower replica id
+    const double dd = __dmul_rn(__dsub_rn(qt[a], qt[b]), __dsub_rn(qu[a], qu[b]));
+    const bool ok = dd >= 0.0 || uni[min(a, b)] < exp(dd);
     if (partner_out) {
       partner_out[ga] = b;
       partner_out[gb] = a;
     }
-    S.pair_att[E.pair_off + q] += 1;
+    S.pair_att[pair_off + q] = n_att + 1;
     if (ok) {
-      S.pair_acc[E.pair_off + q] += 1;
+      S.pair_acc[pair_off + q] = n_acc + 1;
       if (acc_out) acc_out[ga] = acc_out[gb] = 1;
       const double sa = sqrt(Tb / Ta), sb = sqrt(Ta / Tb);
-      const double Ka = S.K[ga], Kb = S.K[gb];
       const double Kan = Ka * (sa * sa), Kbn = Kb * (sb * sb);
-      S.vscale[ga] *= sa;
-      S.vscale[gb] *= sb;
-      S.econs[ga] += Ka - Kan;
-      S.econs[gb] += Kb - Kbn;
+      S.vscale[ga] = va * sa;
+      S.vscale[gb] = vb * sb;
+      double ea = Ea + (Ka - Kan), eb = Eb + (Kb - Kbn);
       S.K[ga] = Kan;
       S.K[gb] = Kbn;
       S.T[ga] = Tb;
@@ -394,16 +446,27 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
         const double Uan = Ua * ua, Ubn = Ub * ub;
         S.fscale[ga] *= ua;
         S.fscale[gb] *= ub;
-        S.econs[ga] += Ua - Uan;
-        S.econs[gb] += Ub - Ubn;
+        ea += Ua - Uan;
+        eb += Ub - Ubn;
         S.U[ga] = Uan;
         S.U[gb] = Ubn;
         S.lam[ga] = lb;
         S.lam[gb] = la;
       }
+      S.econs[ga] = ea;
+      S.econs[gb] = eb;
     }
   }
   __syncthreads();
+  if (rec) {
+    for (int a = threadIdx.x; a < R; a += blockDim.x) {
+      const int g = base + a;
+      rec[g] = S.T[g];
+      rec[rtot + g] = S.U[g];
+      rec[2 * rtot + g] = S.K[g];
+      rec[3 * rtot + g] = S.econs[g];
+    }
+  }
   if (threadIdx.x == 0) S.attempt[blockIdx.x] = attempt + 1;
 }
 
@@ -823,15 +886,16 @@ cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, 
 }
 
 cudaError_t launch_exchange(const StateDev& s, const EnsDev* d_ens, int n_ens, int max_r,
-                            int32_t* d_partner, uint8_t* d_acc, cudaStream_t st) {
-  const size_t smem = sort_keys_bytes(max_r);
+                            int32_t* d_partner, uint8_t* d_acc, cudaStream_t st, double* d_rec,
+                            int rtot) {
+  const size_t smem = exchange_smem_bytes(max_r);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(exchange_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int threads = max_r >= 512 ? 512 : ((max_r + 31) / 32) * 32;
-  exchange_kernel<<<n_ens, threads, smem, st>>>(s, d_ens, d_partner, d_acc);
+  exchange_kernel<<<n_ens, threads, smem, st>>>(s, d_ens, d_partner, d_acc, d_rec, rtot);
   return cudaGetLastError();
 }
 
