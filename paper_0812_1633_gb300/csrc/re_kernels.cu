@@ -79,9 +79,19 @@ __global__ void init_lattice_kernel(StateDev S, const EnsDev* __restrict__ ens,
   const double scale = sqrt(S.T[r] / (2.0 * K / nf));
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const int g = rd.atom_off + i;
-    S.vx[g] *= scale;
-    S.vy[g] *= scale;
-    S.vz[g] *= scale;
+    const double vx = S.vx[g] * scale, vy = S.vy[g] * scale, vz = S.vz[g] * scale;
+    if (S.vfix) {
+      vfix_put(S.vx, g, vfix_from_double(vx));
+      vfix_put(S.vy, g, vfix_from_double(vy));
+      vfix_put(S.vz, g, vfix_from_double(vz));
+      hfix_put(S.fx, g, 0.0f);
+      hfix_put(S.fy, g, 0.0f);
+      hfix_put(S.fz, g, 0.0f);
+    } else {
+      S.vx[g] = vx;
+      S.vy[g] = vy;
+      S.vz[g] = vz;
+    }
   }
   if (threadIdx.x == 0) {
     S.K[r] = K * scale * scale;
@@ -341,10 +351,15 @@ __host__ __device__ inline size_t sort_keys_bytes(int R) {
 // all keys, broadcast reads, no barriers); longer ones by sort_keys.
 constexpr int kRankSortMax = 256;
 
-// shared memory of exchange_kernel for R replicas: sort_keys' area, then per
-// replica the quotients lam/T and U/lam, the exchange uniform, T and lam
+// shared memory of exchange_kernel for R replicas: sort_keys' area (12 bytes
+// per key slot: not a multiple of 8 for a one-replica ladder), then, from the
+// next 16-byte boundary, per replica the quotients lam/T and U/lam, the
+// exchange uniform, T and lam
+__host__ __device__ inline size_t exchange_dbl_offset(int R) {
+  return (sort_keys_bytes(R) + 15) / 16 * 16;
+}
 __host__ __device__ inline size_t exchange_smem_bytes(int R) {
-  return sort_keys_bytes(R) + (size_t)R * 5 * sizeof(double);
+  return exchange_dbl_offset(R) + (size_t)R * 5 * sizeof(double);
 }
 
 // One exchange attempt per ensemble (one CTA each): ladder keys T/lam sorted,
@@ -371,7 +386,7 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
   while (m < R) m <<= 1;
   double* key = reinterpret_cast<double*>(sh);
   int* order = reinterpret_cast<int*>(key + m);
-  double* qt = reinterpret_cast<double*>(sh + sort_keys_bytes(R));  // lam / T
+  double* qt = reinterpret_cast<double*>(sh + exchange_dbl_offset(R));  // lam / T
   double* qu = qt + R;                                               // U / lam
   double* uni = qu + R;                                              // uniform of id a
   double* Tsh = uni + R;
@@ -557,6 +572,16 @@ __global__ void apply_vscale_kernel(StateDev S, const RepDev* __restrict__ reps,
   if (vs == 1.0 && fs == 1.0) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int g = rd.atom_off + i;
+    if (S.vfix) {
+      // the same words and rounding as the batched kernel's launch start
+      vfix_put(S.vx, g, vfix_scale(vfix_get(S.vx, g), vs));
+      vfix_put(S.vy, g, vfix_scale(vfix_get(S.vy, g), vs));
+      vfix_put(S.vz, g, vfix_scale(vfix_get(S.vz, g), vs));
+      hfix_put(S.fx, g, hfix_scale(hfix_get(S.fx, g), fs));
+      hfix_put(S.fy, g, hfix_scale(hfix_get(S.fy, g), fs));
+      hfix_put(S.fz, g, hfix_scale(hfix_get(S.fz, g), fs));
+      continue;
+    }
     S.vx[g] *= vs;
     S.vy[g] *= vs;
     S.vz[g] *= vs;
@@ -593,14 +618,15 @@ __global__ void export_kernel(StateDev S, const EnsDev* __restrict__ ens,
       }
     }
     if (v) {
-      v[3 * o + 0] = S.vx[g];
-      v[3 * o + 1] = S.vy[g];
-      v[3 * o + 2] = S.vz[g];
+      v[3 * o + 0] = S.vfix ? vfix_to_double(vfix_get(S.vx, g)) : S.vx[g];
+      v[3 * o + 1] = S.vfix ? vfix_to_double(vfix_get(S.vy, g)) : S.vy[g];
+      v[3 * o + 2] = S.vfix ? vfix_to_double(vfix_get(S.vz, g)) : S.vz[g];
     }
     if (f) {
-      f[3 * o + 0] = S.fx[g];
-      f[3 * o + 1] = S.fy[g];
-      f[3 * o + 2] = S.fz[g];
+      // mixed path: F = (dt/2 F) / (dt/2), the half-kick increment scaled back
+      f[3 * o + 0] = S.vfix ? (double)hfix_get(S.fx, g) * E.kc.inv_hdt : S.fx[g];
+      f[3 * o + 1] = S.vfix ? (double)hfix_get(S.fy, g) * E.kc.inv_hdt : S.fy[g];
+      f[3 * o + 2] = S.vfix ? (double)hfix_get(S.fz, g) * E.kc.inv_hdt : S.fz[g];
     }
   }
 }
@@ -621,9 +647,15 @@ __global__ void import_kernel(StateDev S, const EnsDev* __restrict__ ens,
       S.qz[g] = fix_from_double(x[3 * o + 2], inv_l);
     }
     if (v) {
-      S.vx[g] = v[3 * o + 0];
-      S.vy[g] = v[3 * o + 1];
-      S.vz[g] = v[3 * o + 2];
+      if (S.vfix) {
+        vfix_put(S.vx, g, vfix_from_double(v[3 * o + 0]));
+        vfix_put(S.vy, g, vfix_from_double(v[3 * o + 1]));
+        vfix_put(S.vz, g, vfix_from_double(v[3 * o + 2]));
+      } else {
+        S.vx[g] = v[3 * o + 0];
+        S.vy[g] = v[3 * o + 1];
+        S.vz[g] = v[3 * o + 2];
+      }
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
