@@ -85,6 +85,9 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
   const int valid0 = S.valid[r];
   const double vs0 = S.vscale[r];
   const double fs0 = S.fscale[r];
+  // factors of exactly 1 (the rule), tested on the integer units
+  const bool vs_one = __double_as_longlong(vs0) == 0x3FF0000000000000LL;
+  const bool fs_one = __double_as_longlong(fs0) == 0x3FF0000000000000LL;
   // the replica's stored energies (U, K, econs), kept by thread 0 of each CTA
   // in shared memory (CTA 0's are written back); registers are kept for the
   // per-atom state
@@ -161,15 +164,16 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
     ref_r[j] = 0;
     if (own && d < 3) {
       xq[j] = qcomp(S, d)[g];
-      const double vv = vcomp(S, d)[g] * vs0;
-      const double ff = fcomp(S, d)[g] * fs0;
       ref(j) = rcomp(S, d)[g];
       if (FP64) {
-        v[j] = vv;
-        f[j] = ff;
+        v[j] = vcomp(S, d)[g] * vs0;
+        f[j] = fcomp(S, d)[g] * fs0;
       } else {
-        vq[j] = __double2ll_rn(vv * 0x1.0p48);  // once per launch
-        hf[j] = (float)(ff * K.hdt);
+        // the state is stored in these words: FP64 only for a pending factor
+        const long long vb = vfix_get(vcomp(S, d), g);
+        const float hb = hfix_get(fcomp(S, d), g);
+        vq[j] = vs_one ? vb : vfix_scale(vb, vs0);
+        hf[j] = fs_one ? hb : hfix_scale(hb, fs0);
       }
     }
   }
@@ -717,8 +721,8 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
         vcomp(S, d)[g] = v[j];
         fcomp(S, d)[g] = f[j];
       } else {
-        vcomp(S, d)[g] = (double)vq[j] * 0x1.0p-48;
-        fcomp(S, d)[g] = (double)hf[j] * K.inv_hdt;
+        vfix_put(vcomp(S, d), g, vq[j]);
+        hfix_put(fcomp(S, d), g, hf[j]);
       }
     }
     ncnt[(size_t)i * P + q] = cnt;

@@ -788,6 +788,7 @@ int build_context(re_ctx* c, const std::vector<Ensemble>& es, const std::vector<
                       : 0;
   c->n_atoms = atom_off;
   c->n_nbr = nbr_off;
+  c->s.vfix = (c->opt.path == RE_PATH_BATCHED && c->opt.precision == RE_PREC_MIXED) ? 1 : 0;
   apply_cells(c, c->opt.cell_div);
   c->cfg = default_cfg(c);
   c->cfg.cell_div = c->opt.cell_div;
@@ -1548,7 +1549,7 @@ struct CkptHeader {
   LaunchCfg cfg;
   uint64_t shape;  // hash of the ensembles' parameters and the replica table
 };
-constexpr char kCkptMagic[8] = {'R', 'E', '-', 'C', 'K', 'P', 'T', '2'};
+constexpr char kCkptMagic[8] = {'R', 'E', '-', 'C', 'K', 'P', 'T', '3'};
 
 struct CkptArray {
   void* dev;

@@ -263,4 +263,28 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Velocity and force words of the mixed path's native state (StateDev::vfix):
+// v as 64-bit fixed point in units of 2^-48, the half-kick increment as FP32.
+__device__ __forceinline__ long long vfix_get(const double* a, size_t g) {
+  return reinterpret_cast<const long long*>(a)[g];
+}
+__device__ __forceinline__ void vfix_put(double* a, size_t g, long long vq) {
+  reinterpret_cast<long long*>(a)[g] = vq;
+}
+__device__ __forceinline__ float hfix_get(const double* a, size_t g) {
+  return __uint_as_float((uint32_t)reinterpret_cast<const unsigned long long*>(a)[g]);
+}
+__device__ __forceinline__ void hfix_put(double* a, size_t g, float h) {
+  reinterpret_cast<unsigned long long*>(a)[g] = __float_as_uint(h);
+}
+__device__ __forceinline__ double vfix_to_double(long long vq) { return (double)vq * 0x1.0p-48; }
+__device__ __forceinline__ long long vfix_from_double(double v) {
+  return __double2ll_rn(v * 0x1.0p48);
+}
+// pending factors: v <- v * vs, the half-kick increment (and the force) <- * fs
+__device__ __forceinline__ long long vfix_scale(long long vq, double vs) {
+  return __double2ll_rn((double)vq * vs);
+}
+__device__ __forceinline__ float hfix_scale(float h, double fs) { return (float)((double)h * fs); }
+
 }  // namespace re

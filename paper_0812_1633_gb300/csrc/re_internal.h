@@ -108,6 +108,11 @@ struct StateDev {
                                      // atom held in this slot (atoms are renumbered in space order)
   int32_t* order;                    // per atom: spatial re-sort order (scratch)
   uint64_t* sbuf;                    // 7 words per atom: re-sort staging (scratch)
+  // 1: the v and f arrays hold the mixed kernel's own words (v: 64-bit fixed
+  // point in units of 2^-48; f: the FP32 half-kick increment dt/2 F in the
+  // low 4 bytes), so a launch loads and stores its state without FP64
+  // conversions; 0: doubles (FP64 and plain paths)
+  int vfix;
 };
 
 // Free-running replica exchange inside one persistent launch (Implementation
