@@ -647,6 +647,27 @@ def run_precision(args):
     N, R, S = PREC_N, PREC_R, args.prec_steps
     L = inputs.box_length(N)
     temps = precision_temps()
+    if args.prec_full:
+        # the whole 256-replica ladder on the mixed batched path
+        full = inputs.geometric_ladder(0.75, 1.8, 256)
+        out = {"study": "precision, whole ladder: mixed batched path",
+               "workload": f"256 x {N}, T 0.75-1.8 geometric, rho 0.8442, dt 0.005, tau_T 0.5, "
+                           f"skin 0.5, FCC start, seed {PREC_SEED}", "steps": S}
+        ctx = re.Context(N, L, 2.5, full, PREC_SEED)
+        sl, wall = drift_run(ctx, S, 100, N)
+        ctx.close()
+        out["drift"] = {"slopes": sl.tolist(), "mean": float(np.mean(sl)),
+                        "sd": float(np.std(sl, ddof=1)), "max_abs": float(np.abs(sl).max()),
+                        "replica_atom_steps_per_s": 256 * N * S / wall}
+        print(json.dumps({"drift": out["drift"]}), flush=True)
+        ctx = re.Context(N, L, 2.5, full, PREC_SEED)
+        acc, att, sl, wall = exchange_run(ctx, S // 10, 10, N)
+        ctx.close()
+        out["exchange"] = {"nx": 10, "acceptance_per_pair": acc, "attempts_per_pair": att,
+                           "slopes": sl.tolist(), "mean_slope": float(np.mean(sl)),
+                           "wall_s": wall}
+        print(json.dumps(out), flush=True)
+        return
     out = {"study": "precision: energy drift and exchange acceptance per path",
            "workload": f"{R} consecutive replicas (the coldest) of the 256-replica ladder T "
                        f"0.75-1.8, N {N}, rho 0.8442, dt 0.005, tau_T 0.5, skin 0.5, FCC start, "
@@ -983,6 +1004,8 @@ def main():
     ap.add_argument("--acc-samples", type=int, default=4000)
     ap.add_argument("--acc-attempts", type=int, default=2000)
     ap.add_argument("--prec-steps", type=int, default=100000)
+    ap.add_argument("--prec-full", action="store_true",
+                    help="precision study: the whole 256-replica ladder, mixed path only")
     ap.add_argument("--drift-n", type=int, default=4000)
     ap.add_argument("--drift-r", type=int, default=8)
     ap.add_argument("--drift-steps", type=int, default=20000)
