@@ -347,8 +347,9 @@ __host__ __device__ inline size_t sort_keys_bytes(int R) {
   return m * (sizeof(double) + sizeof(int));
 }
 
-// Ladders up to this size are ordered by counting ranks (every thread scans
-// all keys, broadcast reads, no barriers); longer ones by sort_keys.
+// Ladders up to this size are ordered by one CTA counting ranks (every thread
+// scans all keys, broadcast reads, no barriers); longer ones by
+// exchange_cluster_kernel.
 constexpr int kRankSortMax = 256;
 
 // shared memory of exchange_kernel for R replicas: sort_keys' area (12 bytes
@@ -362,7 +363,8 @@ __host__ __device__ inline size_t exchange_smem_bytes(int R) {
   return exchange_dbl_offset(R) + (size_t)R * 5 * sizeof(double);
 }
 
-// One exchange attempt per ensemble (one CTA each): ladder keys T/lam sorted,
+// One exchange attempt per ensemble (one CTA each; contexts whose longest
+// ladder exceeds kRankSortMax use exchange_cluster_kernel): ladder keys T/lam sorted,
 // pairs (q, q + d) of the ladder (d = 1: sorted neighbours), the Metropolis
 // rule, and on acceptance the parameter sets (T, lam) are swapped: the
 // velocities take the pending factor sqrt(T_new/T_old), the forces
@@ -483,6 +485,127 @@ __global__ void exchange_kernel(StateDev S, const EnsDev* __restrict__ ens, int3
     }
   }
   if (threadIdx.x == 0) S.attempt[blockIdx.x] = attempt + 1;
+}
+
+// Ladders longer than kRankSortMax: one cluster of C CTAs per ensemble
+// (blocks e*C .. e*C + C - 1).  Every CTA reads the whole ladder's keys and
+// ranks its slice of the replicas by counting (G threads per replica, each
+// counting over every G-th key, summed by shuffles), writing each replica's
+// ladder position into the order array of every CTA of the cluster
+// (distributed shared memory); after a cluster barrier each CTA runs the
+// pairs whose lower ladder position lies in its slice, with the arithmetic of
+// exchange_kernel, so the decisions are the same.  A second barrier makes
+// every CTA's updates visible before the record is written and the attempt
+// counted.
+__global__ void exchange_cluster_kernel(StateDev S, const EnsDev* __restrict__ ens,
+                                        int32_t* partner_out, uint8_t* acc_out, double* rec,
+                                        int rtot) {
+  extern __shared__ __align__(16) unsigned char sh[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+  const int e = blockIdx.x / C;
+  const int R = ens[e].R, base = ens[e].rep_off;
+  const int pair_off = ens[e].pair_off, xdist = ens[e].xdist;
+  const int parity_mode = ens[e].parity_mode;
+  const uint64_t seed = ens[e].seed;
+  const int64_t attempt = S.attempt[e];
+  long long* key = reinterpret_cast<long long*>(sh);  // R: T/lam as bit patterns
+  int* order = reinterpret_cast<int*>(key + R);       // R: replica at each ladder position
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int a = tid; a < R; a += nt) {
+    const double T = S.T[base + a], lam = S.lam[base + a];
+    key[a] = __double_as_longlong(lam == 1.0 ? T : T / lam);
+  }
+  const int per = (R + C - 1) / C;
+  const int a0 = min(R, cr * per), a1 = min(R, a0 + per);
+  for (int a = a0 + tid; a < a1; a += nt) {
+    if (partner_out) partner_out[base + a] = -1;
+    if (acc_out) acc_out[base + a] = 0;
+  }
+  __syncthreads();
+  // G threads (consecutive lanes, G a power of two <= 32) per replica
+  int G = 1;
+  while (G < 32 && G * 2 * per <= nt) G *= 2;
+  for (int t0 = 0; t0 < per * G; t0 += nt) {
+    const int t = t0 + tid;
+    const int a = a0 + t / G, part = t % G;
+    const bool mine = t < per * G && a < a1;
+    int rank = 0;
+    if (mine) {
+      const long long ka = key[a];
+      for (int b = part; b < R; b += G) {
+        const long long kb = key[b];
+        rank += (kb < ka) | ((kb == ka) & (b < a));
+      }
+    }
+    for (int o = G / 2; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    if (mine && part == 0)
+      for (int rk = 0; rk < C; ++rk) *cl.map_shared_rank(order + rank, rk) = a;
+  }
+  cl.sync();
+  const int p = pair_offset(parity_mode, seed, attempt);
+  const int d = max(1, xdist);
+  for (int q = a0 + tid; q < a1; q += nt) {
+    const int qb = ladder_partner(q, R, p, d);
+    if (qb <= q) continue;
+    const int a = order[q], b = order[qb];
+    const int ga = base + a, gb = base + b;
+    const long long n_att = S.pair_att[pair_off + q], n_acc = S.pair_acc[pair_off + q];
+    const double Ka = S.K[ga], Kb = S.K[gb], Ea = S.econs[ga], Eb = S.econs[gb];
+    const double va = S.vscale[ga], vb = S.vscale[gb];
+    const double Ta = S.T[ga], Tb = S.T[gb], la = S.lam[ga], lb = S.lam[gb];
+    const double Ua = S.U[ga], Ub = S.U[gb];
+    const double qta = __ddiv_rn(la, Ta), qtb = __ddiv_rn(lb, Tb);
+    const double qua = la == 1.0 ? Ua : __ddiv_rn(Ua, la), qub = lb == 1.0 ? Ub : __ddiv_rn(Ub, lb);
+    const double dd = __dmul_rn(__dsub_rn(qta, qtb), __dsub_rn(qua, qub));
+    bool ok = dd >= 0.0;
+    if (!ok)
+      ok = uniforms(seed, (uint64_t)min(a, b), (uint64_t)attempt, kTagExch, 0ull).u0 < exp(dd);
+    if (partner_out) {
+      partner_out[ga] = b;
+      partner_out[gb] = a;
+    }
+    S.pair_att[pair_off + q] = n_att + 1;
+    if (ok) {
+      S.pair_acc[pair_off + q] = n_acc + 1;
+      if (acc_out) acc_out[ga] = acc_out[gb] = 1;
+      const double sa = sqrt(Tb / Ta), sb = sqrt(Ta / Tb);
+      const double Kan = Ka * (sa * sa), Kbn = Kb * (sb * sb);
+      S.vscale[ga] = va * sa;
+      S.vscale[gb] = vb * sb;
+      double ea = Ea + (Ka - Kan), eb = Eb + (Kb - Kbn);
+      S.K[ga] = Kan;
+      S.K[gb] = Kbn;
+      S.T[ga] = Tb;
+      S.T[gb] = Ta;
+      if (la != lb) {
+        const double ua = lb / la, ub = la / lb;
+        const double Uan = Ua * ua, Ubn = Ub * ub;
+        S.fscale[ga] *= ua;
+        S.fscale[gb] *= ub;
+        ea += Ua - Uan;
+        eb += Ub - Ubn;
+        S.U[ga] = Uan;
+        S.U[gb] = Ubn;
+        S.lam[ga] = lb;
+        S.lam[gb] = la;
+      }
+      S.econs[ga] = ea;
+      S.econs[gb] = eb;
+    }
+  }
+  __threadfence();  // the pairs' global updates, before the record reads them
+  cl.sync();
+  if (rec) {
+    for (int a = a0 + tid; a < a1; a += nt) {
+      const int g = base + a;
+      rec[g] = S.T[g];
+      rec[rtot + g] = S.U[g];
+      rec[2 * rtot + g] = S.K[g];
+      rec[3 * rtot + g] = S.econs[g];
+    }
+  }
+  if (cr == 0 && tid == 0) S.attempt[e] = attempt + 1;
 }
 
 __global__ void exchange_raw_kernel(int R, const double* __restrict__ T,
@@ -920,6 +1043,31 @@ cudaError_t launch_apply_exchange(const StateDev& s, const double* d_in, int R, 
 cudaError_t launch_exchange(const StateDev& s, const EnsDev* d_ens, int n_ens, int max_r,
                             int32_t* d_partner, uint8_t* d_acc, cudaStream_t st, double* d_rec,
                             int rtot) {
+  if (max_r > kRankSortMax) {
+    // one cluster per ensemble: about 128 replicas per CTA, at most 8 CTAs
+    const int C = std::min(8, (max_r + 127) / 128);
+    const int threads = 512;
+    const size_t smem = (size_t)max_r * (sizeof(long long) + sizeof(int));
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(exchange_cluster_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3((unsigned)(n_ens * C));
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, exchange_cluster_kernel, s, d_ens, d_partner, d_acc, d_rec,
+                              rtot);
+  }
   const size_t smem = exchange_smem_bytes(max_r);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(exchange_kernel,

@@ -1,5 +1,6 @@
-"""The exchange step of a context (one CTA per ensemble: ladders of up to 256
-replicas ordered by counting ranks, longer ones by a bitonic sort) against
+"""The exchange step of a context (ladders of up to 256 replicas: one CTA per
+ensemble ordering them by counting ranks; longer ones: a cluster of CTAs per
+ensemble, each ranking a slice of the ladder) against
 the oracle's exchange on the same temperatures, potential scales and
 energies (Implementation section: sort, pair neighbours, Metropolis with the
 lower replica id's uniform, rescale velocities by sqrt(T_new/T_old)):
@@ -158,3 +159,32 @@ def test_run_record_rejects_negative_budgets(re):
         a.run_record(2, bud)
     a.close()
     b.close()
+
+
+def test_group_exchange_with_a_long_ladder_matches_oracle(re):
+    """A group whose longest ladder (300 replicas) takes the cluster form of the
+    exchange, beside a 5-replica ensemble run by the same launch: every
+    ensemble's partners, decisions and temperatures against the oracle's
+    exchange on its own ladder."""
+    specs = [(256, 300, 0.7, 2.5, 71), (256, 5, 0.8, 1.4, 72)]
+    members = [re.Context(N, inputs.box_length(N), 2.5, inputs.geometric_ladder(t0, t1, R), sd)
+               for (N, R, t0, t1, sd) in specs]
+    g = re.Context.group(members)
+    for m in members:
+        m.close()
+    g.advance(4)
+    for attempt in range(3):
+        T, lam = g.temps(), g.lambdas()
+        U = g.energies()[0]
+        pg, ag = g.exchange(outputs=True)
+        Tg = g.temps()
+        off = 0
+        for (N, R, _, _, sd) in specs:
+            sl = slice(off, off + R)
+            Tn, _, po, ao, _, _, _ = O.exchange_h(T[sl], lam[sl], U[sl], sd, attempt, 0, 1)
+            assert np.array_equal(pg[sl], po)
+            assert np.array_equal(ag[sl], ao)
+            assert np.array_equal(Tg[sl], Tn)
+            off += R
+        g.advance(2)
+    g.close()
