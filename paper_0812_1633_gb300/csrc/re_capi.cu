@@ -121,6 +121,8 @@ struct re_ctx {
   cudaStream_t side = nullptr;      // split launch: the wide class runs here
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int32_t* d_budget = nullptr;      // n_rep, per call
+  std::vector<int32_t> h_budget_last;  // what d_budget holds (when budget_cached)
+  bool budget_cached = false;
   int32_t* d_budget_nx = nullptr;   // n_rep, filled with opt.nx
   int32_t* d_budget_run = nullptr;  // n_cycles * n_rep for re_run
   size_t budget_run_cap = 0;
@@ -677,6 +679,7 @@ int refresh(re_ctx* c) {
   if (c->opt.path == RE_PATH_BATCHED) {
     // budget 0 with invalid lists: the kernel's prologue builds lists, forces, U, K
     RE_CUDA(c, cudaMemsetAsync(c->d_budget, 0, sizeof(int32_t) * c->n_rep, c->stream), "memset");
+    c->budget_cached = false;
     return launch_advance(c, c->d_budget, nullptr, 0);
   }
   c->plain_refresh = true;
@@ -1014,15 +1017,22 @@ int re_advance(re_ctx* c, const int32_t* steps) {
   for (int r = 0; r < c->n_rep; ++r)
     if (steps[r] < 0) return fail(c, RE_EINVAL, "steps[%d] is negative", r);
   if (c->opt.path == RE_PATH_PLAIN) return launch_advance(c, nullptr, steps);
-  // stage the budgets in a pinned ring slot, then copy asynchronously
-  const int slot = c->ring_pos;
-  c->ring_pos = (c->ring_pos + 1) % kRing;
-  RE_CUDA(c, cudaEventSynchronize(c->ring_ev[slot]), "ring wait");
-  int32_t* h = c->h_ring + (size_t)slot * c->n_rep;
-  std::memcpy(h, steps, sizeof(int32_t) * c->n_rep);
-  RE_CUDA(c, cudaMemcpyAsync(c->d_budget, h, sizeof(int32_t) * c->n_rep, cudaMemcpyHostToDevice,
-                             c->stream), "upload budgets");
-  RE_CUDA(c, cudaEventRecord(c->ring_ev[slot], c->stream), "ring record");
+  // the device copy of the budgets is kept: a call with the same budgets as
+  // the last upload (the rule for fixed strides) copies nothing
+  const size_t bb = sizeof(int32_t) * (size_t)c->n_rep;
+  if (!c->budget_cached || std::memcmp(c->h_budget_last.data(), steps, bb) != 0) {
+    // stage the budgets in a pinned ring slot, then copy asynchronously
+    const int slot = c->ring_pos;
+    c->ring_pos = (c->ring_pos + 1) % kRing;
+    RE_CUDA(c, cudaEventSynchronize(c->ring_ev[slot]), "ring wait");
+    int32_t* h = c->h_ring + (size_t)slot * c->n_rep;
+    std::memcpy(h, steps, bb);
+    RE_CUDA(c, cudaMemcpyAsync(c->d_budget, h, bb, cudaMemcpyHostToDevice, c->stream),
+            "upload budgets");
+    RE_CUDA(c, cudaEventRecord(c->ring_ev[slot], c->stream), "ring record");
+    c->h_budget_last.assign(steps, steps + c->n_rep);
+    c->budget_cached = true;
+  }
   int mx = 0, mn = INT_MAX;
   for (int r = 0; r < c->n_rep; ++r) {
     mx = std::max(mx, (int)steps[r]);
@@ -1822,6 +1832,7 @@ int re_autotune(re_ctx* c, int steps) {
     cudaMemcpyAsync(b.save, b.dev, b.bytes, cudaMemcpyDeviceToDevice, c->stream);
   }
   std::vector<int32_t> bud(R, steps);
+  c->budget_cached = false;
   RE_CUDA(c, cudaMemcpyAsync(c->d_budget, bud.data(), 4 * R, cudaMemcpyHostToDevice, c->stream),
           "upload");
   // budgets of one step for the untimed list build of every trial

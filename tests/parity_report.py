@@ -48,12 +48,19 @@ def main():
     build.build()
     out = {}
 
-    # forces and potential energy at one configuration (after 50 steps from the lattice)
+    # forces and potential energy at one configuration (after 50 steps from the
+    # lattice); the mixed path at the skins the tuner chooses from, whose longer
+    # lists give longer FP32 sums per sub-list, in its default launch shape
     rows = []
-    for prec in ("fp64", "mixed"):
+    # (and with one thread per atom: one FP32 sum over the whole list, the
+    # shape the tuner picks for the 256 x 4000 and 1024 x 2048 workloads)
+    cases = ([("fp64", 0.5, 0)] + [("mixed", sk, 0) for sk in (0.2, 0.3, 0.5, 0.6)] +
+             [("mixed", sk, 1) for sk in (0.3, 0.6)])
+    for prec, skin, at in cases:
         for N in (256, 864, 2048, 4000):
             L = inputs.box_length(N)
-            ctx = re.Context(N, L, 2.5, [0.8, 1.2], 7, precision=prec)
+            kw = dict(atom_threads=1, cluster=4 if N > 1024 else 1) if at else {}
+            ctx = re.Context(N, L, 2.5, [0.8, 1.2], 7, precision=prec, skin=skin, **kw)
             ctx.advance(50)
             x, _ = ctx.get_state()
             f = ctx.forces()
@@ -64,8 +71,11 @@ def main():
                 ef = max(ef, float(np.sqrt(((f[k * N:(k + 1) * N] - fo) ** 2).sum(1)).max()) / rms(fo))
                 eu = max(eu, abs(U[k] - Uo) / abs(Uo))
                 eun = max(eun, abs(U[k] - Uo) / N)
-            rows.append({"precision": prec, "N": N, "max_force_err_over_rms": ef,
-                         "rel_U_err": eu, "U_err_per_atom": eun})
+            cfg = ctx.config()
+            rows.append({"precision": prec, "skin": skin, "N": N,
+                         "threads_per_atom": cfg["atom_threads"],
+                         "list_entries_per_atom": 0.8442 * 4 / 3 * math.pi * (2.5 + skin) ** 3,
+                         "max_force_err_over_rms": ef, "rel_U_err": eu, "U_err_per_atom": eun})
             ctx.close()
     out["forces_and_U"] = rows
 
