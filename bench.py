@@ -932,13 +932,13 @@ def run_diffusion(args):
 # capture per workload and launch shape (profiles/md_batched_kernel_64x864.md),
 # valid only while the kernel's sources are the ones that were profiled.
 PROFILED_TRAFFIC = {
-    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "8b34f234f83f911c",
-                                 "bytes_per_launch": 14040064 + 3328,
+    ("c1", (2, 2, 2), "mixed"): {"kernel_sha256_16": "11189abfe7b546db",
+                                 "bytes_per_launch": 14125056 + 5120,
                                  # pipe use over the SMs' active cycles (ncu --set full)
-                                 "pipes": {"fma_pct": 25.41, "alu_pct": 41.85, "fp64_pct": 5.12,
-                                           "issue_active_pct": 61.89,
-                                           "smem_wavefronts": 21273541,
-                                           "smem_bank_conflicts": 8760613}},
+                                 "pipes": {"fma_pct": 26.18, "alu_pct": 43.06, "fp64_pct": 3.70,
+                                           "issue_active_pct": 63.31,
+                                           "smem_wavefronts": 21945811,
+                                           "smem_bank_conflicts": 8730754}},
 }
 
 
