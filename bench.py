@@ -947,8 +947,8 @@ def kernel_sources_hash():
     h = hashlib.sha256()
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_0812_1633_gb300",
                         "csrc")
-    for f in ("re_md.cuh", "re_batched.cuh", "re_batched_mix.cu", "re_device.cuh",
-              "re_internal.h"):
+    for f in ("re_md.cuh", "re_batched.cuh", "re_batched_mix.cu", "re_batched_mix_narrow.cu",
+              "re_device.cuh", "re_internal.h"):
         with open(os.path.join(here, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

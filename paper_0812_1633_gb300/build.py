@@ -20,7 +20,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libre_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["re_kernels.cu", "re_capi.cu", "re_noalloc.cu", "re_batched_f64.cu", "re_batched_mix.cu",
-           "re_batched_f64_async.cu", "re_batched_mix_async.cu"]
+           "re_batched_f64_async.cu", "re_batched_mix_async.cu", "re_batched_f64_narrow.cu",
+           "re_batched_mix_narrow.cu", "re_batched_f64_async_narrow.cu",
+           "re_batched_mix_async_narrow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "--expt-relaxed-constexpr"]

@@ -25,8 +25,11 @@ namespace {
 // FP64 path: FP64 state arithmetic and FP64 pair forces throughout.
 // MODE 0: per-replica step budgets; 1: master-stop (dims.async_nx); 2:
 // free-running with exchanges inside the launch (fr).
-template <bool FP64, int P, bool LSM, int MODE>
-__global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
+// MAXT: the most threads per CTA of this instantiation; it sets the register
+// budget (1024: 64 registers per thread; kNarrowThreads = 896: 72), and the
+// launcher picks the narrowest instantiation that holds the launch's CTAs.
+template <bool FP64, int P, bool LSM, int MODE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) md_batched_kernel(StateDev S,
                                                              const EnsDev* __restrict__ ens,
                                                              const RepDev* __restrict__ reps,
                                                              const int* __restrict__ work,
@@ -743,14 +746,14 @@ __global__ void __launch_bounds__(1024, 1) md_batched_kernel(StateDev S,
 
 }  // namespace
 
-template <bool FP64, int P, bool LSM, int MODE>
+template <bool FP64, int P, bool LSM, int MODE, int MAXT>
 cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDev* d_rep,
                                    const int* d_work, int n_work, const int32_t* d_budget,
                                    const LaunchCfg& cfg, int max_n, int max_ncell,
                                    size_t list_elems, int async_nx, cudaStream_t st,
                                    const FreeDev* fr) {
   const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
-  auto fn = md_batched_kernel<FP64, P, LSM, MODE>;
+  auto fn = md_batched_kernel<FP64, P, LSM, MODE, MAXT>;
   cudaFuncAttributes fa{};
   cudaError_t e = cudaFuncGetAttributes(&fa, fn);
   if (e != cudaSuccess) return e;
@@ -784,11 +787,11 @@ cudaError_t launch_batched_t(const StateDev& s, const EnsDev* d_ens, const RepDe
   return e;
 }
 
-template <bool FP64, int P, bool LSM>
+template <bool FP64, int P, bool LSM, int MAXT>
 int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell,
                                  size_t list_elems) {
   const size_t smem = batched_smem_bytes(max_n, max_ncell, cfg.threads, FP64, list_elems);
-  auto fn = md_batched_kernel<FP64, P, LSM, 2>;
+  auto fn = md_batched_kernel<FP64, P, LSM, 2, MAXT>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

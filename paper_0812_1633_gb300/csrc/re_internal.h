@@ -198,9 +198,12 @@ int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int 
   const StateDev &s, const EnsDev *d_ens, const RepDev *d_rep, const int *d_work,        \
       int n_work, const int32_t *d_budget, const LaunchCfg &cfg, int max_n, int max_ncell, \
       size_t list_elems, int async_nx, cudaStream_t st, const FreeDev *fr
-template <bool FP64, int P, bool LSM, int MODE>
+// MAXT: 1024, or kNarrowThreads for launches of at most that many threads
+// per CTA (a larger register budget per thread).
+constexpr int kNarrowThreads = 896;
+template <bool FP64, int P, bool LSM, int MODE, int MAXT>
 cudaError_t launch_batched_t(BATCHED_LAUNCH_ARGS);
-template <bool FP64, int P, bool LSM>
+template <bool FP64, int P, bool LSM, int MAXT>
 int max_active_clusters_t(const LaunchCfg& cfg, int max_n, int max_ncell, size_t list_elems);
 // Work lists of a split launch: replicas ranked by decreasing temperature T
 // (ties by index); the wide_n hottest go to work[R - wide_n .. R), in rank

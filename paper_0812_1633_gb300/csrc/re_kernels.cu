@@ -871,7 +871,10 @@ size_t batched_smem_bytes(int max_n, int max_ncell, int threads, bool fp64, size
 
 
 int batched_max_active_clusters(bool fp64, const LaunchCfg& cfg, int max_n, int max_ncell) {
-#define RE_MC(F, PP) return max_active_clusters_t<F, PP, false>(cfg, max_n, max_ncell, 0);
+#define RE_MC(F, PP)                                                                   \
+  return cfg.threads <= kNarrowThreads                                                   \
+             ? max_active_clusters_t<F, PP, false, kNarrowThreads>(cfg, max_n, max_ncell, 0) \
+             : max_active_clusters_t<F, PP, false, 1024>(cfg, max_n, max_ncell, 0);
 #define RE_MCP(F)             \
   switch (cfg.atom_threads) { \
     case 1: RE_MC(F, 1)       \
@@ -976,8 +979,13 @@ cudaError_t launch_batched(const StateDev& s, const EnsDev* d_ens, const RepDev*
   // the two free-running modes keep the lists in global memory
   if (mode != 0 && lsm) return cudaErrorInvalidValue;
 #define RE_LB(F, PP, LS, M)                                                                   \
-  return launch_batched_t<F, PP, LS, M>(s, d_ens, d_rep, d_work, n_work, d_budget, cfg,      \
-                                        max_n, max_ncell, list_elems, async_nx, st, fr);
+  return cfg.threads <= kNarrowThreads                                                         \
+             ? launch_batched_t<F, PP, LS, M, kNarrowThreads>(s, d_ens, d_rep, d_work, n_work, \
+                                                              d_budget, cfg, max_n, max_ncell, \
+                                                              list_elems, async_nx, st, fr)    \
+             : launch_batched_t<F, PP, LS, M, 1024>(s, d_ens, d_rep, d_work, n_work, d_budget, \
+                                                    cfg, max_n, max_ncell, list_elems,         \
+                                                    async_nx, st, fr);
 #define RE_LBP(F, LS, M)                           \
   switch (cfg.atom_threads) {                      \
     case 1: RE_LB(F, 1, LS, M)                     \
