@@ -181,8 +181,11 @@ int re_run_async(re_ctx *c, int n_cycles, int nx, int use_graph);
  * exactly as re_exchange does.  n_att attempts per ensemble, then the launch
  * ends.
  *
- * Requires the batched path and all replicas resident on the GPU at once
- * (RE_EINVAL otherwise).  Every device wait is bounded (1 s by default,
+ * Requires the batched path and all replicas resident on the GPU at once:
+ * when the tuned launch shape cannot hold them all, the call runs in the first
+ * shape with fewer CTAs per replica (the same threads per atom first, then
+ * fewer) that can, rebuilding the neighbour lists for it and again for the
+ * tuned shape afterwards; RE_EINVAL when no shape can.  Every device wait is bounded (1 s by default,
  * re_set_wait_limit); a wait that gives up ends the launch with RE_ETIMEOUT,
  * reported here when logging or by the next getter.  The launch then leaves
  * every replica at a step boundary with a consistent state: an exchange pair

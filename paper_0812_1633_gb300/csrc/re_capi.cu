@@ -151,6 +151,8 @@ struct re_ctx {
   int32_t* d_log_acc = nullptr;
   int log_rows = 0;
   int resident_clusters = -1;  // batched clusters resident at once (-1: not yet queried)
+  LaunchCfg fcfg{};             // free-running launch when the tuned shape is not resident
+  bool use_fcfg = false;        // set for the duration of such a launch (list layout 2)
   double wait_s = 1.0;         // limit of the free-running exchange's bounded waits
   int stall_rep = -1;          // fault injection for the next re_run_free (-1: none)
   int stall_from = 0;
@@ -560,6 +562,10 @@ int launch_class(re_ctx* c, int e, const int32_t* d_budget, cudaStream_t st, boo
 // new shape(s) with zero budgets.  The replicas' list rebuild counters are
 // kept (this rebuild is a change of layout, not the list rule of the
 // Example section).
+// The lists' layout follows the launch shape's threads per atom.  Layouts:
+// 0 the uniform shape (cfg), 1 the per-ensemble shapes (ecfg), 2 the
+// free-running fallback shape (fcfg).  A switch rebuilds every list (and the
+// forces) at the current positions; rebuild counters are kept.
 int relayout_lists(re_ctx* c, int mode) {
   if (c->list_mode == mode) return RE_OK;
   c->list_mode = mode;
@@ -573,6 +579,10 @@ int relayout_lists(re_ctx* c, int mode) {
       const int rc = launch_class(c, (int)e, c->d_zero, c->stream);
       if (rc) return rc;
     }
+  } else if (mode == 2) {
+    cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, c->d_zero,
+                                       fp64, c->fcfg, c->max_n, c->max_ncell, 0, 0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
   } else {
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, c->d_work, c->n_rep, c->d_zero,
                                        fp64, c->cfg, c->max_n, c->max_ncell, 0, 0, c->stream);
@@ -608,7 +618,8 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
     {
       // a group switching between its per-ensemble launches and the uniform
       // one (free-running modes) rebuilds its lists in the other layout first
-      const int rc = relayout_lists(c, budgets && per_class(c) ? 1 : 0);
+      const bool fshape = !budgets && fr && fr->nx > 0 && c->use_fcfg;
+      const int rc = relayout_lists(c, budgets && per_class(c) ? 1 : (fshape ? 2 : 0));
       if (rc) return rc;
     }
     if (budgets && per_class(c)) {
@@ -654,9 +665,10 @@ int launch_advance(re_ctx* c, const int32_t* d_budget, const int32_t* h_budget,
     if (order)
       RE_CUDA(c, re::launch_order_work(d_budget, c->d_rep, c->d_ens, 0, c->n_rep, c->d_work_ord,
                                        c->stream), "order work");
+    const LaunchCfg& k = (!budgets && fr && fr->nx > 0 && c->use_fcfg) ? c->fcfg : c->cfg;
     cudaError_t e = re::launch_batched(c->s, c->d_ens, c->d_rep, order ? c->d_work_ord : c->d_work,
-                                       c->n_rep, d_budget, fp64, c->cfg, c->max_n, c->max_ncell,
-                                       budgets ? list_elems_for(c, c->cfg) : 0, async_nx,
+                                       c->n_rep, d_budget, fp64, k, c->max_n, c->max_ncell,
+                                       budgets ? list_elems_for(c, k) : 0, async_nx,
                                        c->stream, fr);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched MD launch");
     return RE_OK;
@@ -1041,6 +1053,45 @@ int re_advance(re_ctx* c, const int32_t* steps) {
   return launch_advance(c, c->d_budget, nullptr, mx, 0, nullptr, mn != mx);
 }
 
+namespace {
+
+// The shape of a free-running launch, in which replicas wait for one another:
+// all its clusters must be resident at once.  The tuned shape when it is
+// (*narrower = false); otherwise (fcfg, *narrower = true) the first resident
+// one with fewer CTAs per replica, trying the tuned threads per atom first
+// (same list layout) and then fewer.
+int free_shape(re_ctx* c, bool* narrower) {
+  const bool fp64 = c->opt.precision == RE_PREC_FP64;
+  *narrower = false;
+  if (c->resident_clusters < 0)
+    c->resident_clusters = re::batched_max_active_clusters(fp64, c->cfg, c->max_n, c->max_ncell);
+  if (c->n_rep <= c->resident_clusters) return RE_OK;
+  const std::string err = c->err;
+  const int clusters[5] = {8, 4, 3, 2, 1};
+  const int pvals[4] = {8, 4, 2, 1};
+  for (int cl : clusters) {
+    if (cl >= c->cfg.cluster) continue;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p : pvals) {
+        // pass 0: the tuned threads per atom; pass 1: fewer
+        if (pass == 0 ? p != c->cfg.atom_threads : p >= c->cfg.atom_threads) continue;
+        LaunchCfg k{cl, threads_for(c->max_n, cl, p), c->cfg.cell_div, p, 0, 0, 0, 0, 0};
+        if (k.threads > 1024 || check_cfg(c, k) != RE_OK) continue;
+        if (re::batched_max_active_clusters(fp64, k, c->max_n, c->max_ncell) < c->n_rep) continue;
+        c->err = err;
+        c->fcfg = k;
+        *narrower = true;
+        return RE_OK;
+      }
+  }
+  return fail(c, RE_EINVAL,
+              "free-running exchange needs all %d replicas resident at once; %d clusters of the "
+              "tuned launch shape fit on the GPU, and no shape with fewer CTAs per replica holds "
+              "them all", c->n_rep, c->resident_clusters);
+}
+
+}  // namespace
+
 int re_advance_async(re_ctx* c, int nx) {
   ApiRange range_("re_advance_async");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
@@ -1062,14 +1113,12 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
   if ((int64_t)(n_att + 1) * (16 * (int64_t)nx + 16) > INT32_MAX)
     return fail(c, RE_EINVAL, "n_att * nx too large for one launch");
   // every replica waits for others inside the launch: all clusters must be
-  // resident at once
-  if (c->resident_clusters < 0)
-    c->resident_clusters = re::batched_max_active_clusters(c->opt.precision == RE_PREC_FP64,
-                                                           c->cfg, c->max_n, c->max_ncell);
-  if (c->n_rep > c->resident_clusters)
-    return fail(c, RE_EINVAL,
-                "free-running exchange needs all %d replicas resident at once; %d clusters of "
-                "this launch shape fit on the GPU", c->n_rep, c->resident_clusters);
+  // resident at once -- in the tuned shape, or else in a narrower one
+  bool narrower = false;
+  {
+    const int rc = free_shape(c, &narrower);
+    if (rc) return rc;
+  }
   const int E = (int)c->ens.size(), R = c->n_rep;
   const bool want_log = log_step || log_T || log_partner || log_acc;
   if (!c->d_fr_words) {
@@ -1122,9 +1171,14 @@ int re_run_free(re_ctx* c, int n_att, int nx, int64_t* log_step, double* log_T,
     RE_CUDA(c, cudaMemsetAsync(c->d_log_acc, 0, 4 * n, c->stream), "clear log");
     RE_CUDA(c, cudaMemsetAsync(c->d_log_T, 0, 8 * n, c->stream), "clear log");
   }
+  c->use_fcfg = narrower;
   int rc = launch_advance(c, c->d_budget_nx, nullptr, n_att * nx, 0, &fr);
+  c->use_fcfg = false;
   if (rc) return rc;
   RE_CUDA(c, re::launch_attempt_add(c->s, E, n_att, c->stream), "attempt counters");
+  // back to the tuned shape's list layout (replicas stopped by a failed wait
+  // keep invalid lists and rebuild them at their next launch)
+  if (narrower && (rc = relayout_lists(c, 0))) return rc;
   if (!want_log) return RE_OK;
   // the log is read back also when the launch failed: it shows where every
   // replica stopped

@@ -162,6 +162,35 @@ def test_free_running_mixed_many_replicas(re):
     assert np.isfinite(ctx.energies()[0]).all()
 
 
+def test_free_running_falls_back_to_a_resident_shape(re):
+    """160 replicas in 8-CTA clusters with 8 threads per atom (1280 CTAs) cannot
+    all be resident; the free-running call runs in a narrower shape that can
+    (fewer CTAs and threads per replica, lists rebuilt in its layout) and
+    replays on the oracle; budget cycles afterwards, back in the tuned shape,
+    follow the oracle too."""
+    N, R, seed, nx, A = 256, 160, 43, 10, 6
+    L = inputs.box_length(N)
+    temps = inputs.geometric_ladder(0.8, 1.6, R)
+    ctx = re.Context(N, L, 2.5, temps, seed, precision="fp64", cluster=8, atom_threads=8)
+    ens = O.Ensemble(N, L, temps, seed)
+    steps, T, partner, acc = ctx.run_free(A, nx, log=True)
+    prev = np.zeros(R, np.int64)
+    for k in range(A):
+        made = steps[k] - prev
+        assert (made >= 1).all(), made
+        ens.advance([int(x) for x in made])
+        po, ao = ens.exchange()
+        assert np.array_equal(partner[k], po), k
+        assert np.array_equal(acc[k].astype(bool), ao.astype(bool)), k
+        assert np.array_equal(T[k], ens.temps()), k
+        prev = steps[k].copy()
+    compare(ctx, ens, N, L, tol=1e-9)
+    assert ctx.config()["cluster"] == 8 and ctx.config()["atom_threads"] == 8
+    ctx.advance(7)
+    ens.advance([7] * R)
+    compare(ctx, ens, N, L, tol=1e-9)
+
+
 def test_free_running_refuses_non_resident_launch(re):
     N, R = 256, 1000
     L = inputs.box_length(N)
