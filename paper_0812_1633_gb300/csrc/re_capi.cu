@@ -1233,6 +1233,12 @@ int re_run_async(re_ctx* c, int n_cycles, int nx, int use_graph) {
     return RE_OK;
   };
   if (!use_graph || n_cycles == 0) return enqueue();
+  // master-stop launches use the uniform shape's list layout: switch to it
+  // before the capture, not inside the graph
+  {
+    const int rc = relayout_lists(c, 0);
+    if (rc) return rc;
+  }
   cudaStream_t cap = nullptr;
   RE_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
   cudaStream_t saved = c->stream;
@@ -1344,6 +1350,13 @@ int re_run(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph) {
     return RE_OK;
   };
   if (!use_graph) return enqueue();
+  // the graph's launches expect the budget launches' list layout: restore it
+  // first, outside the graph (a free-running call in between may have
+  // switched it), so that neither a capture nor a replay meets the other one
+  {
+    const int rc = relayout_lists(c, per_class(c) ? 1 : 0);
+    if (rc) return rc;
+  }
   if (!c->graph || c->graph_cycles != n_cycles || c->graph_budget != dbud) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);

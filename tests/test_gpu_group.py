@@ -257,3 +257,55 @@ def test_group_switches_between_launch_layouts(re):
             assert U[r0s[i] + k] == pytest.approx(r.U, rel=1e-10)
             assert steps_now[r0s[i] + k] == r.step
             a0 += N
+
+
+def test_group_graph_replay_after_a_free_running_call(re):
+    """A group with per-ensemble launches captures its budget cycles in a CUDA
+    graph, runs the free-running exchange (which lays the lists out for the
+    uniform launch), then replays the cached graph: the lists must be laid out
+    for the per-ensemble launches again before the replay.  FP64: the whole
+    sequence -- graph cycles, the free-running attempts replayed from their
+    log, graph cycles again -- follows the oracle."""
+    specs = [(256, 4, 0.8, 1.6), (500, 4, 0.8, 1.6)]
+    seed0, nx, A, cyc = 150, 5, 3, 3
+    g = make_group(re, specs, seed0, precision="fp64", nx=nx)
+    assert len(g.config()["classes"]) == 2
+    ens = [O.Ensemble(N, inputs.box_length(N), inputs.geometric_ladder(t0, t1, R), seed0 + i)
+           for i, (N, R, t0, t1) in enumerate(specs)]
+    r0s = np.cumsum([0] + [R for (_, R, _, _) in specs])
+
+    def oracle_cycles(n):
+        for _ in range(n):
+            for e in ens:
+                e.advance([nx] * len(e.reps))
+                e.exchange()
+
+    g.run(cyc, graph=True)
+    oracle_cycles(cyc)
+    base = g.counters()[0]
+    steps, T, partner, acc = g.run_free(A, nx, log=True)
+    for i, e in enumerate(ens):
+        prev = base[r0s[i]:r0s[i + 1]].copy()
+        for k in range(A):
+            st = steps[k, r0s[i]:r0s[i + 1]]
+            e.advance([int(x) for x in st - prev])
+            po, ao = e.exchange()
+            assert np.array_equal(partner[k, r0s[i]:r0s[i + 1]], po), (i, k)
+            prev = st.copy()
+        e.advance([int(x) for x in g.counters()[0][r0s[i]:r0s[i + 1]] - prev])
+    g.run(cyc, graph=True)
+    oracle_cycles(cyc)
+    x, v = g.get_state()
+    U, _, _ = g.energies()
+    assert np.array_equal(g.temps(), np.concatenate([e.temps() for e in ens]))
+    a0 = 0
+    for i, e in enumerate(ens):
+        N = specs[i][0]
+        L = inputs.box_length(N)
+        for k, r in enumerate(e.reps):
+            d = x[a0:a0 + N] - r.x
+            d -= L * np.rint(d / L)
+            assert np.abs(d).max() < 1e-9, (i, k)
+            assert np.abs(v[a0:a0 + N] - r.v).max() < 1e-9, (i, k)
+            assert U[r0s[i] + k] == pytest.approx(r.U, rel=1e-10)
+            a0 += N
