@@ -241,9 +241,13 @@ int re_run(re_ctx *c, int n_cycles, const int32_t *steps, int use_graph);
  * arrived (synchronous).  Outputs (host, n_cycles x n_rep each, row k =
  * cycle k, replica ids as in re_exchange; any may be NULL): partner id (-1:
  * unpaired), accepted flag, temperature after the attempt, U, K and H~ (as
- * re_energies would report after the attempt).  Errors as re_run; a replica
- * error (status) is reported after the last cycle, the outputs written. */
-int re_run_record(re_ctx *c, int n_cycles, const int32_t *steps, int32_t *partner,
+ * re_energies would report after the attempt).  use_graph != 0 captures the
+ * cycles, their copies included, in one CUDA graph, kept for the next call
+ * with the same n_cycles (the budgets are read from the host array at every
+ * call); the batched path only (the plain path runs eagerly).  Errors as
+ * re_run; a replica error (status) is reported after the last cycle, the
+ * outputs written. */
+int re_run_record(re_ctx *c, int n_cycles, const int32_t *steps, int use_graph, int32_t *partner,
                   uint8_t *accepted, double *T, double *U, double *K, double *H);
 
 /* Per replica (host, n_rep each, K and H may be NULL): potential energy U,

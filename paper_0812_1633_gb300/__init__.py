@@ -61,7 +61,7 @@ def lib():
         L.re_advance.argtypes = [vp, i32p]
         L.re_exchange.argtypes = [vp, i32p, u8p]
         L.re_run.argtypes = [vp, C.c_int, i32p, C.c_int]
-        L.re_run_record.argtypes = [vp, C.c_int, i32p, i32p, u8p, dp, dp, dp, dp]
+        L.re_run_record.argtypes = [vp, C.c_int, i32p, C.c_int, i32p, u8p, dp, dp, dp, dp]
         L.re_advance_async.argtypes = [vp, C.c_int]
         L.re_run_async.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.re_run_free.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_int64),
@@ -251,9 +251,10 @@ class Context:
             sp = _p(s, C.c_int32)
         _check(lib().re_run(self._h, int(cycles), sp, 1 if graph else 0), self._h)
 
-    def run_record(self, cycles, steps=None):
+    def run_record(self, cycles, steps=None, graph=False):
         """re_run_record: `cycles` x {advance, exchange} with each cycle's
-        budgets copied in and its record copied out; returns arrays of shape
+        budgets copied in and its record copied out (graph: as one CUDA graph,
+        kept for the next call of the same length); returns arrays of shape
         (cycles, n_rep): partner, accepted, T, U, K, H."""
         n = int(cycles)
         sp = None
@@ -264,7 +265,7 @@ class Context:
                "accepted": np.zeros((n, self.n_rep), np.uint8)}
         for k in ("T", "U", "K", "H"):
             out[k] = np.zeros((n, self.n_rep))
-        _check(lib().re_run_record(self._h, n, sp, _p(out["partner"], C.c_int32),
+        _check(lib().re_run_record(self._h, n, sp, 1 if graph else 0, _p(out["partner"], C.c_int32),
                                    _p(out["accepted"], C.c_uint8), _p(out["T"], C.c_double),
                                    _p(out["U"], C.c_double), _p(out["K"], C.c_double),
                                    _p(out["H"], C.c_double)), self._h)

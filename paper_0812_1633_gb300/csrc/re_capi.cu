@@ -166,6 +166,9 @@ struct re_ctx {
   size_t rec_bud_cap = 0;           // entries of d_rec_bud and h_rec_bud
   cudaStream_t rec_in = nullptr, rec_out = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t rec_graph = nullptr;  // cached graph of re_run_record
+  int rec_graph_cycles = 0;
+  bool rec_graph_steps = false;
   // cached graph of re_run
   cudaGraphExec_t graph = nullptr;
   int graph_cycles = 0;
@@ -1404,7 +1407,7 @@ void dfree_tracked(re_ctx* c, void* p) {
 
 }  // namespace
 
-int re_run_record(re_ctx* c, int n_cycles, const int32_t* steps, int32_t* partner,
+int re_run_record(re_ctx* c, int n_cycles, const int32_t* steps, int use_graph, int32_t* partner,
                   uint8_t* accepted, double* T, double* U, double* K, double* H) {
   ApiRange range_("re_run_record");
   if (!c) return fail(nullptr, RE_EINVAL, "context is NULL");
@@ -1420,6 +1423,10 @@ int re_run_record(re_ctx* c, int n_cycles, const int32_t* steps, int32_t* partne
   const size_t off_part = 32 * R, off_acc = 36 * R;
   if (rowb * n_cycles > c->rec_cap || (steps && !plain && nb > c->rec_bud_cap)) {
     RE_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+    if (c->rec_graph) {  // it holds the addresses of the areas replaced here
+      cudaGraphExecDestroy(c->rec_graph);
+      c->rec_graph = nullptr;
+    }
     if (rowb * n_cycles > c->rec_cap) {
       dfree_tracked(c, c->d_rec);
       c->d_rec = nullptr;
@@ -1453,41 +1460,93 @@ int re_run_record(re_ctx* c, int n_cycles, const int32_t* steps, int32_t* partne
   RE_CUDA(c, cudaStreamSynchronize(c->rec_in), "synchronise");
   RE_CUDA(c, cudaStreamSynchronize(c->rec_out), "synchronise");
   if (steps && !plain) std::memcpy(c->h_rec_bud, steps, sizeof(int32_t) * nb);
-  for (int k = 0; k < n_cycles; ++k) {
-    const int32_t* hrow = steps ? steps + (size_t)k * R : nullptr;
-    int rc;
-    if (plain) {
-      rc = launch_advance(c, nullptr, hrow);
-    } else if (hrow) {
-      int mx = 0, mn = INT_MAX;
-      for (size_t r = 0; r < R; ++r) {
-        mx = std::max(mx, (int)hrow[r]);
-        mn = std::min(mn, (int)hrow[r]);
+  // the cycles: budgets in on rec_in, advance and exchange on the context's
+  // stream, records out on rec_out; both copy streams join the stream at the end
+  auto enqueue = [&]() -> int {
+    for (int k = 0; k < n_cycles; ++k) {
+      const int32_t* hrow = steps ? steps + (size_t)k * R : nullptr;
+      int rc;
+      if (plain) {
+        rc = launch_advance(c, nullptr, hrow);
+      } else if (hrow) {
+        int mx = 0, mn = INT_MAX;
+        for (size_t r = 0; r < R; ++r) {
+          mx = std::max(mx, (int)hrow[r]);
+          mn = std::min(mn, (int)hrow[r]);
+        }
+        // this cycle's budgets: their own copy, which the advance waits for
+        int32_t* drow = c->d_rec_bud + (size_t)k * R;
+        RE_CUDA(c, cudaMemcpyAsync(drow, c->h_rec_bud + (size_t)k * R, sizeof(int32_t) * R,
+                                   cudaMemcpyHostToDevice, c->rec_in), "upload budgets");
+        RE_CUDA(c, cudaEventRecord(c->ev_in, c->rec_in), "event");
+        RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_in, 0), "event wait");
+        rc = launch_advance(c, drow, nullptr, mx, 0, nullptr, mn != mx);
+      } else {
+        rc = launch_advance(c, c->d_budget_nx, nullptr, c->opt.nx);
       }
-      // this cycle's budgets: their own copy, which the advance waits for
-      int32_t* drow = c->d_rec_bud + (size_t)k * R;
-      RE_CUDA(c, cudaMemcpyAsync(drow, c->h_rec_bud + (size_t)k * R, sizeof(int32_t) * R,
-                                 cudaMemcpyHostToDevice, c->rec_in), "upload budgets");
-      RE_CUDA(c, cudaEventRecord(c->ev_in, c->rec_in), "event");
-      RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_in, 0), "event wait");
-      rc = launch_advance(c, drow, nullptr, mx, 0, nullptr, mn != mx);
-    } else {
-      rc = launch_advance(c, c->d_budget_nx, nullptr, c->opt.nx);
+      if (rc) return rc;
+      unsigned char* row = c->d_rec + (size_t)k * rowb;
+      cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
+                                          reinterpret_cast<int32_t*>(row + off_part),
+                                          row + off_acc, c->stream,
+                                          reinterpret_cast<double*>(row), (int)R);
+      if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
+      // the record of cycle k travels while cycle k + 1 runs
+      RE_CUDA(c, cudaEventRecord(c->ev_out, c->stream), "event");
+      RE_CUDA(c, cudaStreamWaitEvent(c->rec_out, c->ev_out, 0), "event wait");
+      RE_CUDA(c, cudaMemcpyAsync(c->h_rec + (size_t)k * rowb, row, rowb, cudaMemcpyDeviceToHost,
+                                 c->rec_out), "read record");
     }
+    RE_CUDA(c, cudaEventRecord(c->ev_in, c->rec_in), "event");
+    RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_in, 0), "event wait");
+    RE_CUDA(c, cudaEventRecord(c->ev_out, c->rec_out), "event");
+    RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
+    return RE_OK;
+  };
+  if (!use_graph || plain) {
+    const int rc = enqueue();
     if (rc) return rc;
-    unsigned char* row = c->d_rec + (size_t)k * rowb;
-    cudaError_t e = re::launch_exchange(c->s, c->d_ens, (int)c->ens.size(), c->max_r,
-                                        reinterpret_cast<int32_t*>(row + off_part), row + off_acc,
-                                        c->stream, reinterpret_cast<double*>(row), (int)R);
-    if (e != cudaSuccess) return cuda_fail(c, e, "exchange launch");
-    // the record of cycle k travels while cycle k + 1 runs
-    RE_CUDA(c, cudaEventRecord(c->ev_out, c->stream), "event");
-    RE_CUDA(c, cudaStreamWaitEvent(c->rec_out, c->ev_out, 0), "event wait");
-    RE_CUDA(c, cudaMemcpyAsync(c->h_rec + (size_t)k * rowb, row, rowb, cudaMemcpyDeviceToHost,
-                               c->rec_out), "read record");
+  } else {
+    // the budget launches' list layout, switched outside the graph
+    int rc = relayout_lists(c, per_class(c) ? 1 : 0);
+    if (rc) return rc;
+    if (!c->rec_graph || c->rec_graph_cycles != n_cycles ||
+        c->rec_graph_steps != (steps != nullptr)) {
+      if (c->rec_graph) {
+        cudaGraphExecDestroy(c->rec_graph);
+        c->rec_graph = nullptr;
+      }
+      cudaStream_t cap = nullptr;
+      RE_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stream");
+      cudaStream_t saved = c->stream;
+      c->stream = cap;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        // the copy streams join the capture through an event of the stream
+        e = cudaEventRecord(c->ev_out, cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rec_in, c->ev_out, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rec_out, c->ev_out, 0);
+        rc = e == cudaSuccess ? enqueue() : cuda_fail(c, e, "graph fork");
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (rc == RE_OK && e2 != cudaSuccess) rc = cuda_fail(c, e2, "graph capture");
+      } else {
+        rc = cuda_fail(c, e, "begin capture");
+      }
+      c->stream = saved;
+      cudaStreamDestroy(cap);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      e = cudaGraphInstantiate(&c->rec_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      c->rec_graph_cycles = n_cycles;
+      c->rec_graph_steps = steps != nullptr;
+    }
+    RE_CUDA(c, cudaGraphLaunch(c->rec_graph, c->stream), "graph launch");
   }
-  RE_CUDA(c, cudaEventRecord(c->ev_out, c->rec_out), "event");
-  RE_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0), "event wait");
   const int rc = status_check(c);  // synchronises the stream, and so the copies
   if (rc != RE_OK && rc != RE_ENUMERIC && rc != RE_EOVERFLOW) return rc;
   for (int k = 0; k < n_cycles; ++k) {
@@ -1766,6 +1825,10 @@ int re_checkpoint_load(re_ctx* c, const void* buf, size_t bytes) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+  }
+  if (c->rec_graph) {
+    cudaGraphExecDestroy(c->rec_graph);
+    c->rec_graph = nullptr;
   }
   size_t off = sizeof h + sizeof(LaunchCfg) * c->ens.size();
   for (const CkptArray& a : ckpt_arrays(c)) {
@@ -2051,6 +2114,10 @@ int re_autotune(re_ctx* c, int steps) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  if (c->rec_graph) {
+    cudaGraphExecDestroy(c->rec_graph);
+    c->rec_graph = nullptr;
+  }
   rc = refresh(c);
   if (rc) return rc;
   return status_check(c);
@@ -2088,6 +2155,7 @@ void re_destroy(re_ctx* c) {
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->h_rec) cudaFreeHost(c->h_rec);
   if (c->h_rec_bud) cudaFreeHost(c->h_rec_bud);
+  if (c->rec_graph) cudaGraphExecDestroy(c->rec_graph);
   if (c->rec_in) cudaStreamDestroy(c->rec_in);
   if (c->rec_out) cudaStreamDestroy(c->rec_out);
   if (c->ev_in) cudaEventDestroy(c->ev_in);

@@ -101,6 +101,26 @@ def test_run_record_equals_the_per_call_api(re, kw):
     b.close()
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(precision="fp64")], ids=["mixed", "fp64"])
+def test_run_record_graph_equals_eager(re, kw):
+    """The graph form of re_run_record: the same records and states as the
+    eager form, also on the next call, which replays the kept graph with new
+    budgets."""
+    a, b = _twins(re, **kw)
+    cycles = 5
+    for call in range(2):
+        bud = inputs.random_budgets(a.n_rep, cycles, 5, 20, 20 + call)
+        ra = a.run_record(cycles, bud, graph=True)
+        rb = b.run_record(cycles, bud)
+        for key in ("partner", "accepted", "T", "U", "K", "H"):
+            assert np.array_equal(ra[key], rb[key]), (call, key)
+    xa, va = a.get_state()
+    xb, vb = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    a.close()
+    b.close()
+
+
 def test_run_record_fp64_follows_the_oracle(re):
     """8 x 256 replicas, FP64, uneven budgets: the record of every cycle
     against the oracle ensemble run with the same budgets."""
