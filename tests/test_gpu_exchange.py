@@ -208,3 +208,26 @@ def test_group_exchange_with_a_long_ladder_matches_oracle(re):
             off += R
         g.advance(2)
     g.close()
+
+
+def test_run_record_graph_of_a_group(re):
+    """A group with per-ensemble launches (forked onto their own streams inside
+    the capture): the graph form of re_run_record equals the eager one, on the
+    capturing call and on a replay with new budgets."""
+    specs = [(256, 4, 0.7, 1.6), (500, 6, 0.8, 2.0)]
+    mk = lambda: re.Context.group([
+        re.Context(N, inputs.box_length(N), 2.5, inputs.geometric_ladder(t0, t1, R), 60 + i)
+        for i, (N, R, t0, t1) in enumerate(specs)])
+    a, b = mk(), mk()
+    assert len(a.config()["classes"]) == 2
+    for call in range(2):
+        bud = inputs.random_budgets(a.n_rep, 3, 5, 15, 30 + call)
+        ra = a.run_record(3, bud, graph=True)
+        rb = b.run_record(3, bud)
+        for key in ("partner", "accepted", "T", "H"):
+            assert np.array_equal(ra[key], rb[key]), (call, key)
+    xa, _ = a.get_state()
+    xb, _ = b.get_state()
+    assert np.array_equal(xa, xb)
+    a.close()
+    b.close()
